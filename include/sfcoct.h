@@ -1,0 +1,195 @@
+/*
+ * sfcoct.h - C ABI of the GB300 space-filling-curve linear-octree neighbour search.
+ *
+ * The library implements, on one CUDA device, the data-parallel path of the method of
+ * "Efficient Neighbourhood Search in 3D Point Clouds Through Space-Filling Curves and
+ * Linear Octrees" (arXiv 2603.06771):
+ *   encode every point with a 63-bit Morton or Hilbert code (section 4, 4.1, 4.2),
+ *   reorder the cloud by code (section 4), build the linear octree over the sorted codes
+ *   (section 5.1: leaves, counts, internal nodes, internalRanges), then answer all-points
+ *   or arbitrary-centre fixed-radius searches with the four kernels of section 3.2
+ *   (neighboursPrune / neighboursLin of section 5.1) and kNN searches (section 3.3).
+ *
+ * Conventions shared by every call:
+ *   - Points and centres are float32 xyz triples stored contiguously (array of n x 3
+ *     floats, "AoS").  Pointers marked "device" must be CUDA device (or managed) memory
+ *     of the current device; a host pointer gives SFC_ERR_NOT_DEVICE_PTR.  There is no
+ *     CPU fallback.
+ *   - Every call is asynchronous on cuda_stream (a cudaStream_t; NULL = legacy default
+ *     stream) unless its comment names a synchronisation.
+ *   - Indices returned to the caller (neighbour ids, kNN ids) are positions in the
+ *     caller's original point array, so results do not depend on the encoding.
+ *   - Errors are returned as sfc_status; no exception crosses the ABI.  After
+ *     SFC_ERR_CUDA, sfc_last_error() gives the CUDA message of the calling thread.
+ *   - Sizes: 0 <= n <= 2^31 - 1 points; the node table must fit int32 indices.
+ */
+#ifndef SFCOCT_H
+#define SFCOCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfc_octree_s* sfc_octree; /* opaque handle, owned by the library */
+
+/* Ordering of the cloud (section 4).  SFC_ENC_NONE keeps the cloud in input order: the
+ * octree is still built over Morton codes (a linear octree needs sorted codes, section
+ * 7.1), but the coordinates are not gathered and the searches read them through the
+ * permutation, and all-points queries run in input order. */
+typedef enum { SFC_ENC_NONE = 0, SFC_ENC_MORTON = 1, SFC_ENC_HILBERT = 2 } sfc_encoding;
+
+/* Search kernels, section 3.2 (Definition), all with the strict "<":
+ *   SPHERE ||p - c||_2 < r;  CIRCLE ||(p - c)_xy||_2 < r;
+ *   CUBE ||p - c||_inf < r;  SQUARE ||(p - c)_xy||_inf < r. */
+typedef enum { SFC_SPHERE = 0, SFC_CIRCLE = 1, SFC_CUBE = 2, SFC_SQUARE = 3 } sfc_kernel;
+
+typedef enum {
+    SFC_OK = 0,
+    SFC_ERR_INVALID = 1,         /* bad argument: n < 0, k < 1, NaN radius, bad enum, ... */
+    SFC_ERR_OOM = 2,             /* a device allocation failed */
+    SFC_ERR_CUDA = 3,            /* a CUDA call failed; see sfc_last_error() */
+    SFC_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up (reserved) */
+    SFC_ERR_TOO_LARGE = 5,       /* a size limit of this library is exceeded */
+    SFC_ERR_NOT_DEVICE_PTR = 6,  /* a pointer that must be device memory is not */
+    SFC_ERR_NOT_FINITE = 7,      /* a coordinate, or the cloud's extent, is NaN or infinite */
+    SFC_ERR_INTERNAL = 8         /* a device-side consistency guard tripped (a library bug) */
+} sfc_status;
+
+/* Build options.  leaf_capacity is N_max of sections 3.1 and 5.1 (a leaf above level 21
+ * holds at most N_max points); prune selects neighboursPrune (1: an octant that lies
+ * inside the kernel is taken whole, step 1a of section 5.1) or neighboursLin (0: every
+ * candidate point is tested).  Both give identical results. */
+typedef struct {
+    int32_t leaf_capacity; /* >= 1, default 32 */
+    int32_t prune;         /* 0 or 1, default 1 */
+} sfc_build_opts;
+
+/* Compressed sparse rows: row q holds the neighbours of centre q in
+ * cols[row_ptr[q] .. row_ptr[q + 1]), listed in ascending position along the curve
+ * (ascending sorted position of the tree points).  Device memory. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    int64_t* row_ptr; /* n_rows + 1 entries */
+    int32_t* cols;    /* nnz entries, original point indices */
+} sfc_csr;
+
+typedef struct {
+    int64_t n_points;
+    int64_t n_leaves;   /* 7 * n_internal + 1 (complete octree) */
+    int64_t n_internal;
+    int64_t n_nodes;    /* n_internal + n_leaves */
+    int32_t encoding;
+    int32_t leaf_capacity;
+    int32_t prune;
+    int32_t device;
+    float lo[3];        /* lower corner of the bounding box (section 4, step 1) */
+    float scale;        /* 2^21 / largest extent, binary32 (section 4, step 1) */
+} sfc_octree_info;
+
+/* Fills *opts with the defaults (leaf_capacity 32, prune 1). */
+sfc_status sfc_build_opts_default(sfc_build_opts* opts);
+
+/* Build the octree of n points (sections 4 and 5.1).
+ *   points_xyz  device, n x 3 float32, read only; the library copies what it keeps, so the
+ *               caller may free it once the stream has passed this call.
+ *   n           number of points, 0 <= n <= 2^31 - 1 (n = 0 gives an empty tree).
+ *   enc         SFC_ENC_NONE / MORTON / HILBERT.
+ *   opts        NULL for the defaults.
+ *   out         receives the handle; release it with octree_free.
+ * Steps on the device: bounding box and scale, 63-bit codes (bit 63 is 0), stable LSD
+ * radix sort of (code, index), gather of the sorted cloud, leaves/counts, internal nodes,
+ * internalRanges and a tight bounding box per node.
+ * Synchronises cuda_stream once (to size the node table).  Returns SFC_ERR_NOT_FINITE if a
+ * coordinate is NaN or infinite or the extent overflows binary32. */
+sfc_status octree_build(const float* points_xyz, int64_t n, sfc_encoding enc, const sfc_build_opts* opts,
+                        void* cuda_stream, sfc_octree* out);
+
+/* Release the handle; its device memory is freed in stream order on cuda_stream.  Work
+ * that uses the handle on other streams must be complete or ordered before that stream. */
+sfc_status octree_free(sfc_octree h, void* cuda_stream);
+
+/* Sizes and parameters of a built octree (host struct, no synchronisation). */
+sfc_status octree_info(sfc_octree h, sfc_octree_info* info);
+
+/* Fixed-radius search (section 3.2 kernels; section 5.1 neighboursPrune / neighboursLin).
+ *   queries_xyz  device, n_queries x 3 float32 centres; any finite position, inside the
+ *                cloud's box or not.  NULL = every point of the tree, in the caller's
+ *                original order (then n_queries must be 0 or the number of points).
+ *   r            radius (for CUBE / SQUARE the half side); r <= 0 gives empty rows, a
+ *                NaN r gives SFC_ERR_INVALID.
+ *   out          receives a CSR whose two arrays the library allocates with
+ *                cudaMallocAsync on cuda_stream; release it with sfc_csr_free.
+ * Row q lists every tree point p with kernel(p, centre q, r) true, the centre itself
+ * included when it is a tree point.  Synchronises cuda_stream once (to read nnz). */
+sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                         void* cuda_stream, sfc_csr* out);
+
+/* The two halves of radius_search for callers that allocate the output themselves.
+ * radius_count writes row_ptr (device, n_rows + 1 int64, caller-owned) and *nnz (host);
+ * it synchronises cuda_stream once.  radius_fill then writes cols (device, *nnz int32,
+ * caller-owned) given the same queries, r and kernel and that row_ptr. */
+sfc_status radius_count(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                        void* cuda_stream, int64_t* row_ptr, int64_t* nnz);
+sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                       void* cuda_stream, const int64_t* row_ptr, int32_t* cols);
+
+/* Free a CSR allocated by radius_search (stream ordered); zeroes *csr. */
+sfc_status sfc_csr_free(sfc_csr* csr, void* cuda_stream);
+
+/* k nearest neighbours (section 3.3) under the squared Euclidean distance in binary32,
+ * d2 = (dx*dx + dy*dy) + dz*dz with d = p - c, each operation rounded to nearest.
+ *   queries_xyz  as for radius_search (NULL = all tree points, original order).
+ *   k            1 <= k <= 64.
+ *   out_idx      device, n_rows x k int32, caller-owned: original point indices.
+ *   out_d2       device, n_rows x k float32, caller-owned.
+ * Row q is sorted by (d2, index) ascending, so equal distances go to the smaller index;
+ * when k exceeds the number of points the row is padded with index -1 and d2 = +inf.
+ * With queries_xyz == NULL the call does not synchronise; with caller centres it
+ * synchronises once to report non-finite centres (SFC_ERR_NOT_FINITE). */
+sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_queries, int32_t k, void* cuda_stream,
+               int32_t* out_idx, float* out_d2);
+
+/* ---- introspection (tests, diagnostics) ------------------------------------------ */
+
+/* Copy the sorted codes (n), the permutation sorted position -> original index (n), the
+ * leaves array (n_leaves + 1, last entry 8^21) and the per-leaf point counts (n_leaves)
+ * into caller-owned device buffers; any pointer may be NULL. */
+sfc_status octree_export(sfc_octree h, void* cuda_stream, uint64_t* sorted_keys, uint32_t* perm,
+                         uint64_t* leaves, uint32_t* leaf_counts);
+
+/* Copy the node table (n_nodes entries; node 0 is the root, the eight children of an
+ * internal node are consecutive): first code of the node's cell, level (0..21),
+ * internalRanges [start, end) in sorted positions, first-child index (-1 for a leaf) and
+ * tight bounding box (lo xyz, hi xyz; +inf/-inf when empty).  Caller-owned device
+ * buffers; any pointer may be NULL. */
+sfc_status octree_export_nodes(sfc_octree h, void* cuda_stream, uint64_t* node_key, int32_t* node_level,
+                               uint32_t* node_start, uint32_t* node_end, int32_t* node_child, float* node_box);
+
+/* 63-bit codes of integer cells (sections 4.1, 4.2) at L = 21: cells device n x 3 uint32
+ * (each < 2^21), keys device n uint64.  SFC_ENC_NONE gives Morton codes. */
+sfc_status sfc_encode_cells(const uint32_t* cells, int64_t n, sfc_encoding enc, void* cuda_stream,
+                            uint64_t* keys);
+
+/* ---- runtime ------------------------------------------------------------------------ */
+
+const char* sfc_status_string(sfc_status s);
+/* Last CUDA error message seen by the calling thread ("" if none). */
+const char* sfc_last_error(void);
+/* Number of kernels this library has launched in this process. */
+uint64_t sfc_launch_count(void);
+/* Per-kernel timing with CUDA events recorded on each launch's stream: on != 0 starts a
+ * new record, 0 stops recording. */
+sfc_status sfc_profile_enable(int32_t on);
+/* Synchronises on the recorded events and returns the number of distinct kernels
+ * recorded; for i < min(that, cap): names[i * 64 ..] (NUL-terminated), launches[i],
+ * total_ms[i]. */
+int32_t sfc_profile_read(char* names, int64_t* launches, double* total_ms, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFCOCT_H */

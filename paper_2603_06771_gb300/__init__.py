@@ -1,0 +1,14 @@
+"""GB300-native space-filling-curve linear-octree neighbour search (arXiv 2603.06771).
+
+The compute path is the CUDA library ``libsfcoct.so`` (sources in ``csrc/``, C ABI in
+``include/sfcoct.h``); this package builds it (:mod:`.build`) and binds it with ctypes
+(:mod:`.binding`).  See ``octree_build``, ``radius_search`` and ``knn``.
+"""
+from .binding import (ENCODINGS, KERNELS, Octree, SFCError, encode_cells, knn, launch_count, library_path,
+                      octree_build, profile_enable, profile_read, radius_count, radius_fill, radius_search,
+                      radius_search_csr)
+from .build import build
+
+__all__ = ["ENCODINGS", "KERNELS", "Octree", "SFCError", "build", "encode_cells", "knn", "launch_count",
+           "library_path", "octree_build", "profile_enable", "profile_read", "radius_count", "radius_fill",
+           "radius_search", "radius_search_csr"]

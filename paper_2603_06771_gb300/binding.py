@@ -1,0 +1,311 @@
+"""ctypes binding of ``libsfcoct.so`` (the C ABI in ``include/sfcoct.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels.
+PyTorch provides device memory and the current stream.  If the library has not been
+built, or a call fails, a Python exception is raised; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from .build import LIB
+
+__all__ = [
+    "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
+    "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
+]
+
+ENCODINGS = {"none": 0, "morton": 1, "hilbert": 2}
+KERNELS = {"sphere": 0, "circle": 1, "cube": 2, "square": 3}
+
+SFC_OK = 0
+STATUS_NAMES = {0: "SFC_OK", 1: "SFC_ERR_INVALID", 2: "SFC_ERR_OOM", 3: "SFC_ERR_CUDA", 4: "SFC_ERR_TIMEOUT",
+                5: "SFC_ERR_TOO_LARGE", 6: "SFC_ERR_NOT_DEVICE_PTR", 7: "SFC_ERR_NOT_FINITE"}
+
+
+class SFCError(RuntimeError):
+    def __init__(self, status: int, call: str, detail: str = ""):
+        self.status = status
+        msg = f"{call} failed: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class _BuildOpts(C.Structure):
+    _fields_ = [("leaf_capacity", C.c_int32), ("prune", C.c_int32)]
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("cols", C.c_void_p)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_leaves", C.c_int64), ("n_internal", C.c_int64),
+                ("n_nodes", C.c_int64), ("encoding", C.c_int32), ("leaf_capacity", C.c_int32),
+                ("prune", C.c_int32), ("device", C.c_int32), ("lo", C.c_float * 3), ("scale", C.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGNATURES = {
+    "sfc_build_opts_default": (C.c_int, [C.c_void_p]),
+    "octree_build": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "octree_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "octree_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "radius_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int, C.c_void_p, C.c_void_p]),
+    "radius_count": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    "radius_fill": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int, C.c_void_p, C.c_void_p,
+                              C.c_void_p]),
+    "sfc_csr_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "knn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "octree_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "octree_export_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
+    "sfc_encode_cells": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "sfc_status_string": (C.c_char_p, [C.c_int]),
+    "sfc_last_error": (C.c_char_p, []),
+    "sfc_launch_count": (C.c_uint64, []),
+    "sfc_profile_enable": (C.c_int, [C.c_int32]),
+    "sfc_profile_read": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+}
+
+
+def library_path() -> str:
+    return LIB
+
+
+def lib():
+    """The loaded library; raises if ``libsfcoct.so`` has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is missing: build it with paper_2603_06771_gb300.build.build()")
+            L = C.CDLL(LIB)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(status: int, call: str):
+    if status != SFC_OK:
+        detail = lib().sfc_last_error().decode() if status == 3 else ""
+        raise SFCError(status, call, detail)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _enc(encoding) -> int:
+    return ENCODINGS[encoding] if isinstance(encoding, str) else int(encoding)
+
+
+def _kern(kernel) -> int:
+    return KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+
+
+def _xyz(t: torch.Tensor | None, what: str) -> torch.Tensor | None:
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 3):
+        raise ValueError(f"{what} must be a CUDA float32 tensor of shape (n, 3)")
+    return t.contiguous()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None or t.numel() == 0 else C.c_void_p(t.data_ptr())
+
+
+class Octree:
+    """A built linear octree (handle of the C ABI).  Release with :meth:`free`."""
+
+    def __init__(self, handle: C.c_void_p, stream):
+        self._h = handle
+        self._stream = stream
+        info = _Info()
+        _check(lib().octree_info(self._h, C.byref(info)), "octree_info")
+        self.n = int(info.n_points)
+        self.n_leaves = int(info.n_leaves)
+        self.n_internal = int(info.n_internal)
+        self.n_nodes = int(info.n_nodes)
+        self.encoding = int(info.encoding)
+        self.leaf_capacity = int(info.leaf_capacity)
+        self.prune = bool(info.prune)
+        self.lo = tuple(float(v) for v in info.lo)
+        self.scale = float(info.scale)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("octree already freed")
+        return self._h
+
+    def free(self, stream=None):
+        if self._h is not None:
+            _check(lib().octree_free(self._h, C.c_void_p(_stream(stream))), "octree_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None and lib() is not None:
+                lib().octree_free(self._h, C.c_void_p(_stream(self._stream)))
+                self._h = None
+        except Exception:
+            pass
+
+    def export(self, stream=None) -> dict:
+        """Sorted codes, permutation, leaves array and leaf counts as CUDA tensors."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        keys = torch.empty(self.n, dtype=torch.int64, device=dev)
+        perm = torch.empty(self.n, dtype=torch.int32, device=dev)
+        leaves = torch.empty(self.n_leaves + 1, dtype=torch.int64, device=dev)
+        counts = torch.empty(self.n_leaves, dtype=torch.int32, device=dev)
+        _check(lib().octree_export(self.handle, C.c_void_p(_stream(stream)), _ptr(keys), _ptr(perm), _ptr(leaves),
+                                   _ptr(counts)), "octree_export")
+        return {"keys": keys, "perm": perm, "leaves": leaves, "counts": counts}
+
+    def export_nodes(self, stream=None) -> dict:
+        """Node table: code, level, [start, end), first child (-1 leaf), tight box."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        m = self.n_nodes
+        out = {"key": torch.empty(m, dtype=torch.int64, device=dev),
+               "level": torch.empty(m, dtype=torch.int32, device=dev),
+               "start": torch.empty(m, dtype=torch.int32, device=dev),
+               "end": torch.empty(m, dtype=torch.int32, device=dev),
+               "child": torch.empty(m, dtype=torch.int32, device=dev),
+               "box": torch.empty((m, 6), dtype=torch.float32, device=dev)}
+        _check(lib().octree_export_nodes(self.handle, C.c_void_p(_stream(stream)), _ptr(out["key"]),
+                                         _ptr(out["level"]), _ptr(out["start"]), _ptr(out["end"]),
+                                         _ptr(out["child"]), _ptr(out["box"])), "octree_export_nodes")
+        return out
+
+
+def octree_build(points: torch.Tensor, encoding="hilbert", leaf_capacity: int = 32, prune: bool = True,
+                 stream=None) -> Octree:
+    """``octree_build`` of the C ABI: encode, sort, gather and link the linear octree."""
+    pts = _xyz(points, "points")
+    opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
+    h = C.c_void_p()
+    s = _stream(stream)
+    _check(lib().octree_build(_ptr(pts), pts.shape[0], _enc(encoding), C.byref(opts), C.c_void_p(s), C.byref(h)),
+           "octree_build")
+    return Octree(h, stream)
+
+
+def radius_count(tree: Octree, queries: torch.Tensor | None, r: float, kernel="sphere", stream=None):
+    """Row pointers (int64 CUDA tensor, rows + 1) and the neighbour total."""
+    q = _xyz(queries, "queries")
+    rows = tree.n if q is None else q.shape[0]
+    row_ptr = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
+    nnz = C.c_int64()
+    _check(lib().radius_count(tree.handle, _ptr(q), 0 if q is None else rows, C.c_float(r), _kern(kernel),
+                              C.c_void_p(_stream(stream)), _ptr(row_ptr), C.byref(nnz)), "radius_count")
+    return row_ptr, int(nnz.value)
+
+
+def radius_fill(tree: Octree, queries: torch.Tensor | None, r: float, kernel, row_ptr: torch.Tensor, nnz: int,
+                stream=None) -> torch.Tensor:
+    q = _xyz(queries, "queries")
+    cols = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    rows = tree.n if q is None else q.shape[0]
+    _check(lib().radius_fill(tree.handle, _ptr(q), 0 if q is None else rows, C.c_float(r), _kern(kernel),
+                             C.c_void_p(_stream(stream)), _ptr(row_ptr), _ptr(cols)), "radius_fill")
+    return cols[:nnz]
+
+
+def radius_search(tree: Octree, queries: torch.Tensor | None, r: float, kernel="sphere", stream=None):
+    """CSR (row_ptr int64, cols int32) of the fixed-radius search, torch-allocated."""
+    row_ptr, nnz = radius_count(tree, queries, r, kernel, stream)
+    return row_ptr, radius_fill(tree, queries, r, kernel, row_ptr, nnz, stream)
+
+
+class _DeviceArray:
+    """Exposes library-owned device memory through ``__cuda_array_interface__``."""
+
+    def __init__(self, owner, ptr: int, n: int, typestr: str):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "stream": None}
+
+
+class _CsrOwner:
+    def __init__(self, csr: _Csr, stream: int):
+        self.csr = csr
+        self.stream = stream
+
+    def __del__(self):
+        try:
+            lib().sfc_csr_free(C.byref(self.csr), C.c_void_p(self.stream))
+        except Exception:
+            pass
+
+
+def radius_search_csr(tree: Octree, queries: torch.Tensor | None, r: float, kernel="sphere", stream=None):
+    """``radius_search`` of the C ABI (library-allocated CSR) viewed as torch tensors."""
+    q = _xyz(queries, "queries")
+    rows = tree.n if q is None else q.shape[0]
+    csr = _Csr()
+    s = _stream(stream)
+    _check(lib().radius_search(tree.handle, _ptr(q), 0 if q is None else rows, C.c_float(r), _kern(kernel),
+                               C.c_void_p(s), C.byref(csr)), "radius_search")
+    owner = _CsrOwner(csr, s)
+    row_ptr = torch.as_tensor(_DeviceArray(owner, csr.row_ptr, csr.n_rows + 1, "<i8"), device="cuda")
+    cols = torch.as_tensor(_DeviceArray(owner, csr.cols, csr.nnz, "<i4"), device="cuda")
+    return row_ptr, cols
+
+
+def knn(tree: Octree, queries: torch.Tensor | None, k: int, stream=None):
+    """(idx int32 [rows, k], d2 float32 [rows, k]) of the k nearest points."""
+    q = _xyz(queries, "queries")
+    rows = tree.n if q is None else q.shape[0]
+    idx = torch.empty((rows, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((rows, k), dtype=torch.float32, device="cuda")
+    _check(lib().knn(tree.handle, _ptr(q), 0 if q is None else rows, int(k), C.c_void_p(_stream(stream)),
+                     _ptr(idx), _ptr(d2)), "knn")
+    return idx, d2
+
+
+def encode_cells(cells: torch.Tensor, encoding="hilbert", stream=None) -> torch.Tensor:
+    """63-bit codes (int64 tensor) of integer cells (n, 3) < 2^21."""
+    if not (cells.is_cuda and cells.dim() == 2 and cells.shape[1] == 3 and cells.dtype == torch.int32):
+        raise ValueError("cells must be a CUDA int32 tensor of shape (n, 3)")
+    cells = cells.contiguous()
+    keys = torch.empty(cells.shape[0], dtype=torch.int64, device=cells.device)
+    _check(lib().sfc_encode_cells(_ptr(cells), cells.shape[0], _enc(encoding), C.c_void_p(_stream(stream)),
+                                  _ptr(keys)), "sfc_encode_cells")
+    return keys
+
+
+def launch_count() -> int:
+    return int(lib().sfc_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check(lib().sfc_profile_enable(1 if on else 0), "sfc_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded since profile_enable."""
+    cap = 256
+    names = C.create_string_buffer(64 * cap)
+    launches = (C.c_int64 * cap)()
+    ms = (C.c_double * cap)()
+    n = lib().sfc_profile_read(names, launches, ms, cap)
+    out = {}
+    for i in range(min(n, cap)):
+        name = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (int(launches[i]), float(ms[i]))
+    return out

@@ -1,0 +1,243 @@
+// sfc_internal.cuh - types and helpers shared by the translation units of libsfcoct.
+//
+// Layout of a built octree in device memory (one allocation per array):
+//   pts    float4[n]   sorted cloud: x, y, z and the original index (uint32 bits) in w.
+//                      For SFC_ENC_NONE: the cloud in input order (w = input index).
+//   perm   uint32[n]   sorted position -> original index.
+//   keys   uint64[n]   sorted 63-bit codes.
+//   nodes  NodeBox[m]  m = 1 + 8 * n_internal: node 0 is the root; the eight children
+//                      of the internal node of pre-order rank g are nodes 1 + 8g .. 8 + 8g.
+//                      lo.xyz / hi.xyz = tight box of the node's points, lo.w / hi.w =
+//                      internalRanges [start, end) as uint32 bits.
+//   child  int32[m]    first child of an internal node, -1 for a leaf.
+//   node_key uint64[m], node_level uint8[m]: the node's cell (first code, level).
+//   leaves uint64[nL + 1], leaf_counts uint32[nL]: the leaves array of section 5.1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "sfcoct.h"
+
+namespace sfc {
+
+constexpr int kLevels = 21;                        // L of section 4
+constexpr uint64_t kWholeRange = 1ull << 63;       // 8^21 codes
+constexpr uint32_t kCellMax = (1u << kLevels) - 1;
+constexpr int kMaxK = 64;                          // largest k of the kNN kernels
+constexpr int kStackDepth = 160;                   // >= 7 * 21 + 8 pending nodes of a depth-first walk
+constexpr unsigned int kGuardTripped = 4u;          // BuildScalars::bad bit set by a failed guard
+
+struct __align__(16) NodeBox {
+    float4 lo;  // w: start (uint32 bits)
+    float4 hi;  // w: end (uint32 bits)
+};
+
+// Device-resident scalars of one build.
+struct BuildScalars {
+    unsigned int mn[3];  // order-preserving uint images of the per-axis minima
+    unsigned int mx[3];
+    unsigned int bad;    // bit 0: a coordinate is not finite, bit 1: the extent is not finite,
+                         // bit 2: a consistency guard of a search kernel tripped
+    float lo[3];
+    float scale;
+    float ext;
+};
+
+struct Octree {
+    int device = 0;
+    int64_t n = 0;
+    int enc = 0;
+    int leaf_cap = 32;
+    int prune = 1;
+    float4* pts = nullptr;
+    uint32_t* perm = nullptr;
+    uint64_t* keys = nullptr;
+    NodeBox* nodes = nullptr;
+    int32_t* child = nullptr;
+    uint64_t* node_key = nullptr;
+    uint8_t* node_level = nullptr;
+    uint64_t* leaves = nullptr;
+    uint32_t* leaf_counts = nullptr;
+    BuildScalars* scal = nullptr;
+    int64_t n_internal = 0, n_nodes = 0, n_leaves = 0;
+    float lo[3] = {0, 0, 0};
+    float scale = 1;
+};
+
+// ---------------------------------------------------------------------------------
+// runtime (sfc_runtime.cu)
+void record_cuda_error(cudaError_t e, const char* where);
+// Called around every kernel launch: counts launches, records profiling events.
+void launch_begin(const char* name, cudaStream_t s);
+sfc_status launch_end(const char* name, cudaStream_t s);
+bool is_device_ptr(const void* p);
+sfc_status ensure_pool(int device);
+
+// Stream-ordered scratch allocations, released (in stream order) when the guard dies.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    ~Scratch();
+    template <typename T>
+    sfc_status alloc(T** p, size_t count) {
+        void* v = nullptr;
+        cudaError_t e = cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s_);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "cudaMallocAsync");
+            *p = nullptr;
+            return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
+        }
+        ptrs_.push_back(v);
+        *p = static_cast<T*>(v);
+        return SFC_OK;
+    }
+    // Hand an allocation over to the caller (it is no longer freed by the guard).
+    void release(const void* p);
+    cudaStream_t stream() const { return s_; }
+
+  private:
+    cudaStream_t s_;
+    std::vector<void*> ptrs_;
+};
+
+template <typename T>
+sfc_status dev_alloc(T** p, size_t count, cudaStream_t s) {
+    void* v = nullptr;
+    cudaError_t e = cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s);
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "cudaMallocAsync");
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
+    }
+    *p = static_cast<T*>(v);
+    return SFC_OK;
+}
+void dev_free(void* p, cudaStream_t s);
+
+// Exclusive scans: out[0] = 0, out[i + 1] = out[i] + in[i], out has n + 1 entries.
+// in and out may alias (in-place) when they have the same type.
+sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
+sfc_status scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
+
+// Stable LSD radix sort of (key, value) pairs by the low 63 bits of key; the result ends
+// in keys / vals, keys_alt / vals_alt are work buffers of the same size.
+sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                            cudaStream_t s, Scratch& scratch);
+
+// Centres of a search in processing order: float4 (x, y, z, output row bits).  For
+// queries == NULL the tree points themselves; otherwise caller centres, sorted by their
+// code under the tree's transform for the sorted encodings.  *bad (device) gets bit 0
+// set for a non-finite centre.
+sfc_status prepare_queries(const Octree* h, const float* queries, int64_t nq, cudaStream_t s, Scratch& scratch,
+                           const float4** q4, unsigned int* bad);
+
+#define SFC_TRY(expr)                      \
+    do {                                   \
+        sfc_status st_ = (expr);           \
+        if (st_ != SFC_OK) return st_;     \
+    } while (0)
+
+#define SFC_CUDA(expr)                                        \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) {                              \
+            ::sfc::record_cuda_error(e_, #expr);              \
+            return SFC_ERR_CUDA;                              \
+        }                                                     \
+    } while (0)
+
+#define SFC_LAUNCH(name, stream, kernel, grid, block, smem, ...)   \
+    do {                                                           \
+        ::sfc::launch_begin(name, stream);                         \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__); \
+        SFC_TRY(::sfc::launch_end(name, stream));                  \
+    } while (0)
+
+inline unsigned int grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return static_cast<unsigned int>(g);
+}
+
+// ---------------------------------------------------------------------------------
+// device helpers
+
+// Number of leading octal digits (levels) two 63-bit codes share, 0..21.
+__device__ __forceinline__ int common_levels(uint64_t a, uint64_t b) {
+    uint64_t x = a ^ b;
+    if (x == 0) return kLevels;
+    return (__clzll(static_cast<long long>(x)) - 1) / 3;
+}
+
+// Mask of the code bits below level l (the 3 * (21 - l) low bits).
+__device__ __forceinline__ uint64_t below_level_mask(int l) {
+    return (1ull << (3 * (kLevels - l))) - 1ull;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t n, uint64_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Order-preserving map float -> uint32 (for atomic min / max of floats).
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned int lanes_below() {
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Discretisation of one coordinate (section 4, steps 1-2): floor((p - lo) * s) in
+// binary32, each operation rounded to nearest, clamped into [0, 2^21 - 1].
+__device__ __forceinline__ uint32_t cell_of(float p, float lo, float s) {
+    float f = floorf(__fmul_rn(__fsub_rn(p, lo), s));
+    if (!(f > 0.0f)) return 0u;
+    if (f >= static_cast<float>(kCellMax)) return kCellMax;
+    return static_cast<uint32_t>(f);
+}
+
+// Kernel tests of section 3.2 on d = p - c (each component already rounded), strict "<".
+// No fused multiply-add: every product and sum is rounded on its own.
+template <int KERN>
+__device__ __forceinline__ bool kernel_holds(float dx, float dy, float dz, float r, float r2) {
+    if (KERN == SFC_SPHERE) {
+        float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        return __fadd_rn(s, __fmul_rn(dz, dz)) < r2;
+    } else if (KERN == SFC_CIRCLE) {
+        return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) < r2;
+    } else if (KERN == SFC_CUBE) {
+        return fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz)) < r;
+    } else {
+        return fmaxf(fabsf(dx), fabsf(dy)) < r;
+    }
+}
+
+// Squared Euclidean distance used by kNN: (dx*dx + dy*dy) + dz*dz, rounded per operation.
+__device__ __forceinline__ float sq_dist(float dx, float dy, float dz) {
+    float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return __fadd_rn(s, __fmul_rn(dz, dz));
+}
+
+}  // namespace sfc
+
+// the opaque handle of the C ABI
+struct sfc_octree_s {
+    sfc::Octree tree;
+};

@@ -1,0 +1,328 @@
+// sfc_knn.cu - k nearest neighbours over the linear octree (section 3.3).
+//
+// The paper pops octants and points from one priority queue ordered by distance.  Here
+// each centre keeps its k best (squared distance, original index) pairs in registers,
+// sorted, and the octree is walked depth first with the children of a node visited
+// nearest first; a node is entered only while its box could still hold a better pair.
+// The result is the same exact set, in the same (d2, index) order:
+//   - an octant's lower bound is the squared distance to its box point nearest to the
+//     centre (the clamp of section 3.3), computed with the same rounded operations as a
+//     point distance; rounding is monotone, so no point of the box is nearer;
+//   - a node is skipped only when that bound exceeds the current k-th distance, so a
+//     point tying the k-th distance (which may win on a smaller index) is still seen.
+// For a cloud ordered along the curve a warp serves 32 consecutive centres with one
+// shared walk (a node is entered when any lane needs it); for the unordered cloud each
+// lane walks alone.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "sfc_internal.cuh"
+
+namespace sfc {
+
+constexpr int kKnnWarps = 4;
+constexpr uint32_t kNoIndex = 0xffffffffu;
+
+struct KnnArgs {
+    const float4* __restrict__ pts;
+    const uint32_t* __restrict__ perm;
+    const NodeBox* __restrict__ nodes;
+    const int32_t* __restrict__ child;
+    const float4* __restrict__ q;
+    int64_t nq;
+    int k;
+    int32_t* out_idx;
+    float* out_d2;
+    unsigned int* err;
+    int64_t max_steps;
+};
+
+__device__ __forceinline__ float box_lower_bound(const NodeBox& b, float cx, float cy, float cz) {
+    return sq_dist(__fsub_rn(fminf(fmaxf(cx, b.lo.x), b.hi.x), cx), __fsub_rn(fminf(fmaxf(cy, b.lo.y), b.hi.y), cy),
+                   __fsub_rn(fminf(fmaxf(cz, b.lo.z), b.hi.z), cz));
+}
+
+__device__ __forceinline__ bool pair_less(float da, uint32_t ia, float db, uint32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// Sorted list of the KMAX best pairs; insert keeps it sorted and drops the largest.
+template <int KMAX>
+struct BestList {
+    float d[KMAX];
+    uint32_t i[KMAX];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) {
+            d[s] = INFINITY;
+            i[s] = kNoIndex;
+        }
+    }
+    __device__ __forceinline__ void insert(float nd, uint32_t ni) {
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) {
+            const bool before = pair_less(nd, ni, d[s], i[s]);
+            const float td = d[s];
+            const uint32_t ti = i[s];
+            d[s] = before ? nd : td;
+            i[s] = before ? ni : ti;
+            nd = before ? td : nd;
+            ni = before ? ti : ni;
+        }
+    }
+    // the k-th best pair (k <= KMAX)
+    __device__ __forceinline__ void kth(int k, float* kd, uint32_t* ki) const {
+        float rd = d[0];
+        uint32_t ri = i[0];
+#pragma unroll
+        for (int s = 1; s < KMAX; ++s)
+            if (s == k - 1) {
+                rd = d[s];
+                ri = i[s];
+            }
+        *kd = rd;
+        *ki = ri;
+    }
+    __device__ __forceinline__ void store(const KnnArgs& a, uint32_t row) const {
+        const int64_t base = static_cast<int64_t>(row) * a.k;
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s)
+            if (s < a.k) {
+                a.out_idx[base + s] = i[s] == kNoIndex ? -1 : static_cast<int32_t>(i[s]);
+                a.out_d2[base + s] = d[s];
+            }
+    }
+};
+
+// children order key: empty children last, then by bound, then by child number
+__device__ __forceinline__ uint64_t child_order_key(const NodeBox& cb, float gx, float gy, float gz, int ci) {
+    const bool empty = __float_as_uint(cb.lo.w) == __float_as_uint(cb.hi.w);
+    const uint32_t bound = empty ? 0xffffffffu : float_to_ordered(box_lower_bound(cb, gx, gy, gz));
+    return (static_cast<uint64_t>(bound) << 32) | static_cast<uint32_t>(ci);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kKnnWarps * 32) k_knn_group(KnnArgs a) {
+    __shared__ int32_t stack[kKnnWarps][kStackDepth];
+    const unsigned int lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    int32_t* stk = stack[warp];
+    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kKnnWarps + warp) * 32;
+    if (first >= a.nq) return;
+    const int64_t qi = first + lane;
+    const bool active = qi < a.nq;
+    const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t row = __float_as_uint(c.w);
+
+    // centre of the group, used only to order the walk
+    const unsigned int act = __ballot_sync(0xffffffffu, active);
+    const float inv = 1.0f / static_cast<float>(__popc(act));
+    float gx = active ? c.x : 0.f, gy = active ? c.y : 0.f, gz = active ? c.z : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    }
+    gx *= inv; gy *= inv; gz *= inv;
+
+    BestList<KMAX> best;
+    best.init();
+    float kd = INFINITY;
+    uint32_t ki = kNoIndex;
+
+    bool guard_ok = true;
+    int sp = 1;
+    if (lane == 0) stk[0] = 0;
+    __syncwarp();
+    for (int64_t steps = 0; sp > 0; ++steps) {
+        if (steps >= a.max_steps) {
+            guard_ok = false;
+            break;
+        }
+        --sp;
+        const int32_t node = stk[sp];
+        __syncwarp();
+        const NodeBox b = a.nodes[node];
+        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
+        if (start == end) continue;
+        const bool need = active && box_lower_bound(b, c.x, c.y, c.z) <= kd;
+        if (!__ballot_sync(0xffffffffu, need)) continue;
+        const int32_t fc = a.child[node];
+        if (fc >= 0) {
+            // order the eight children nearest first (bitonic sort over lanes 0..7)
+            uint64_t key = ~0ull;
+            if (lane < 8) key = child_order_key(a.nodes[fc + lane], gx, gy, gz, static_cast<int>(lane));
+#pragma unroll
+            for (int size = 2; size <= 8; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const uint64_t other = __shfl_xor_sync(0xffffffffu, key, stride);
+                    const bool ascending = (lane & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    const bool take = (lower == ascending) ? (other < key) : (other > key);
+                    if (lane < 8 && take) key = other;
+                }
+            }
+            const bool valid = lane < 8 && (key >> 32) != 0xffffffffull;
+            const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+            if (sp + nvalid <= kStackDepth) {
+                if (valid) stk[sp + nvalid - 1 - static_cast<int>(lane)] = fc + static_cast<int32_t>(key & 7ull);
+                sp += nvalid;
+            } else {
+                guard_ok = false;
+            }
+            __syncwarp();
+        } else {
+            for (uint32_t j = start; j < end; ++j) {
+                const float4 p = __ldg(&a.pts[j]);
+                const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
+                const uint32_t id = __float_as_uint(p.w);
+                if (need && pair_less(d, id, kd, ki)) {
+                    best.insert(d, id);
+                    best.kth(a.k, &kd, &ki);
+                }
+            }
+        }
+    }
+    if (active) best.store(a, row);
+    if (!guard_ok && lane == 0) atomicOr(a.err, kGuardTripped);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
+    const int64_t qi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (qi >= a.nq) return;
+    const float4 c = a.q[qi];
+    const uint32_t row = __float_as_uint(c.w);
+    BestList<KMAX> best;
+    best.init();
+    float kd = INFINITY;
+    uint32_t ki = kNoIndex;
+    int32_t stk[kStackDepth];
+    int sp = 1;
+    stk[0] = 0;
+    bool guard_ok = true;
+    for (int64_t steps = 0; sp > 0; ++steps) {
+        if (steps >= a.max_steps) {
+            guard_ok = false;
+            break;
+        }
+        const int32_t node = stk[--sp];
+        const NodeBox b = a.nodes[node];
+        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
+        if (start == end) continue;
+        if (box_lower_bound(b, c.x, c.y, c.z) > kd) continue;
+        const int32_t fc = a.child[node];
+        if (fc >= 0) {
+            uint64_t keys[8];
+#pragma unroll
+            for (int ci = 0; ci < 8; ++ci) keys[ci] = child_order_key(a.nodes[fc + ci], c.x, c.y, c.z, ci);
+            // insertion sort, descending, so that the nearest child is pushed last
+#pragma unroll
+            for (int x = 1; x < 8; ++x)
+#pragma unroll
+                for (int y = x; y > 0; --y)
+                    if (keys[y] > keys[y - 1]) {
+                        const uint64_t t = keys[y]; keys[y] = keys[y - 1]; keys[y - 1] = t;
+                    }
+#pragma unroll
+            for (int ci = 0; ci < 8; ++ci)
+                if ((keys[ci] >> 32) != 0xffffffffull) {
+                    if (sp < kStackDepth) stk[sp++] = fc + static_cast<int32_t>(keys[ci] & 7ull);
+                    else guard_ok = false;
+                }
+        } else {
+            for (uint32_t j = start; j < end; ++j) {
+                const uint32_t id = a.perm[j];
+                const float4 p = a.pts[id];
+                const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
+                if (pair_less(d, id, kd, ki)) {
+                    best.insert(d, id);
+                    best.kth(a.k, &kd, &ki);
+                }
+            }
+        }
+    }
+    best.store(a, row);
+    if (!guard_ok) atomicOr(a.err, kGuardTripped);
+}
+
+template <int KMAX>
+static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) {
+    if (t->enc == SFC_ENC_NONE) {
+        SFC_LAUNCH("knn", s, k_knn_lane<KMAX>, grid_for(a.nq, 128), 128, 0, a);
+    } else {
+        SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for((a.nq + 31) / 32, kKnnWarps), kKnnWarps * 32, 0, a);
+    }
+    return SFC_OK;
+}
+
+__global__ void k_knn_pad(int32_t* idx, float* d2, int64_t total) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
+        idx[i] = -1;
+        d2[i] = INFINITY;
+    }
+}
+
+}  // namespace sfc
+
+extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_queries, int32_t k, void* cuda_stream,
+                          int32_t* out_idx, float* out_d2) {
+    if (!h || k < 1) return SFC_ERR_INVALID;
+    if (k > sfc::kMaxK) return SFC_ERR_TOO_LARGE;
+    const sfc::Octree* t = &h->tree;
+    int64_t rows;
+    if (!queries_xyz) {
+        if (n_queries != 0 && n_queries != t->n) return SFC_ERR_INVALID;
+        rows = t->n;
+    } else {
+        if (n_queries < 0) return SFC_ERR_INVALID;
+        if (n_queries > 0x7fffffffLL - 1) return SFC_ERR_TOO_LARGE;
+        if (n_queries > 0 && !sfc::is_device_ptr(queries_xyz)) return SFC_ERR_NOT_DEVICE_PTR;
+        rows = n_queries;
+    }
+    if (rows == 0) return SFC_OK;
+    if (!out_idx || !out_d2) return SFC_ERR_INVALID;
+    if (!sfc::is_device_ptr(out_idx) || !sfc::is_device_ptr(out_d2)) return SFC_ERR_NOT_DEVICE_PTR;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc::Scratch scratch(s);
+    unsigned int* bad = nullptr;
+    if (queries_xyz) {
+        SFC_TRY(scratch.alloc(&bad, 1));
+        SFC_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), s));
+    }
+    const float4* q4 = nullptr;
+    SFC_TRY(sfc::prepare_queries(t, queries_xyz, rows, s, scratch, &q4, bad));
+    if (t->n == 0) {
+        SFC_LAUNCH("knn_pad", s, sfc::k_knn_pad, sfc::grid_for(rows * k, 256, 152 * 16), 256, 0, out_idx, out_d2,
+                   rows * k);
+    } else {
+        sfc::KnnArgs a;
+        a.pts = t->pts;
+        a.perm = t->perm;
+        a.nodes = t->nodes;
+        a.child = t->child;
+        a.q = q4;
+        a.nq = rows;
+        a.k = k;
+        a.out_idx = out_idx;
+        a.out_d2 = out_d2;
+        a.err = &t->scal->bad;
+        a.max_steps = t->n_nodes;
+        if (k <= 8) SFC_TRY(sfc::launch_knn<8>(t, a, s));
+        else if (k <= 16) SFC_TRY(sfc::launch_knn<16>(t, a, s));
+        else if (k <= 32) SFC_TRY(sfc::launch_knn<32>(t, a, s));
+        else SFC_TRY(sfc::launch_knn<64>(t, a, s));
+    }
+    if (bad) {
+        unsigned int hbad = 0, herr = 0;
+        SFC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        SFC_CUDA(cudaStreamSynchronize(s));
+        if (hbad) return SFC_ERR_NOT_FINITE;
+        if (herr & sfc::kGuardTripped) return SFC_ERR_INTERNAL;
+    }
+    return SFC_OK;
+}

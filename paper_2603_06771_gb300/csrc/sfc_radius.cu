@@ -1,0 +1,429 @@
+// sfc_radius.cu - fixed-radius search over the linear octree (section 3.2 kernels,
+// section 5.1 neighboursPrune / neighboursLin), compacted into CSR by a count pass, an
+// exclusive scan and a fill pass that repeats the count pass's decisions exactly.
+//
+// Work layout.  For a cloud ordered along the curve, a warp takes 32 consecutive
+// centres in curve order (they are close in space) and walks the octree once for all of
+// them: one lane per centre, the node stack shared in shared memory, a node entered when
+// any lane's kernel may reach its box.  Leaf points are read with warp-uniform loads and
+// tested by every lane against its own centre; hits become a 32-bit mask per lane, and
+// the warp writes each lane's hits as one contiguous run of its output row.  For the
+// unordered cloud (SFC_ENC_NONE) the 32 centres of a warp are scattered, so each lane
+// walks the tree on its own and reads points through the permutation.
+//
+// Exactness of the box tests.  Each node stores the tight bounding box of its points.
+// Rounding to nearest is monotone, so with d = fl(p - c) per axis: the box point
+// nearest to c (the clamp of section 3.3) has the smallest |d| on every axis, and one of
+// the two faces has the largest.  Every kernel test is monotone in |dx|, |dy|, |dz|, so
+// when the nearest box point fails the test every point of the box fails it (prune,
+// step 1b), and when the farthest corner passes every point passes (take the whole range,
+// step 1a).  Both shortcuts therefore give exactly the per-point result.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "sfc_internal.cuh"
+
+namespace sfc {
+
+constexpr int kRadiusWarps = 4;
+
+struct RadiusArgs {
+    const float4* __restrict__ pts;     // sorted cloud (ordered encodings) or input order (NONE)
+    const uint32_t* __restrict__ perm;  // sorted position -> original index
+    const NodeBox* __restrict__ nodes;
+    const int32_t* __restrict__ child;
+    const float4* __restrict__ q;       // centres in processing order, w = output row
+    int64_t nq;
+    float r, r2;
+    int prune;
+    uint32_t* counts;                   // count pass: neighbours per row
+    const int64_t* row_ptr;             // fill pass
+    int32_t* cols;
+    unsigned int* err;                  // kGuardTripped is or-ed in when a guard fails
+    int64_t max_steps;                  // nodes of the tree: a walk pops each node once at most
+};
+
+// 0: no point of the box is inside the kernel; 2: every point is (asked only with
+// prune); 1: undecided.
+template <int KERN>
+__device__ __forceinline__ int classify_box(const NodeBox& b, float cx, float cy, float cz, float r, float r2,
+                                            bool prune) {
+    const float nx = __fsub_rn(fminf(fmaxf(cx, b.lo.x), b.hi.x), cx);
+    const float ny = __fsub_rn(fminf(fmaxf(cy, b.lo.y), b.hi.y), cy);
+    const float nz = __fsub_rn(fminf(fmaxf(cz, b.lo.z), b.hi.z), cz);
+    if (!kernel_holds<KERN>(nx, ny, nz, r, r2)) return 0;
+    if (!prune) return 1;
+    const float fx = fmaxf(fabsf(__fsub_rn(b.lo.x, cx)), fabsf(__fsub_rn(b.hi.x, cx)));
+    const float fy = fmaxf(fabsf(__fsub_rn(b.lo.y, cy)), fabsf(__fsub_rn(b.hi.y, cy)));
+    const float fz = fmaxf(fabsf(__fsub_rn(b.lo.z, cz)), fabsf(__fsub_rn(b.hi.z, cz)));
+    return kernel_holds<KERN>(fx, fy, fz, r, r2) ? 2 : 1;
+}
+
+template <int KERN, bool FILL>
+__global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a) {
+    __shared__ int32_t stack[kRadiusWarps][kStackDepth];
+    const unsigned int lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    int32_t* stk = stack[warp];
+    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp) * 32;
+    if (first >= a.nq) return;  // whole warp
+    const int64_t qi = first + lane;
+    const bool active = qi < a.nq;
+    const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t row = __float_as_uint(c.w);
+    const unsigned int below = lanes_below();
+    const bool prune = a.prune != 0;
+    uint32_t count = 0;
+    int64_t out = (FILL && active) ? a.row_ptr[row] : 0;
+    const int64_t out_end = (FILL && active) ? a.row_ptr[row + 1] : 0;
+    uint32_t taken_below = 0;  // positions below this were emitted as a whole range
+    bool guard_ok = true;
+
+    int sp = 1;
+    if (lane == 0) stk[0] = 0;
+    __syncwarp();
+    for (int64_t steps = 0; sp > 0; ++steps) {
+        if (steps >= a.max_steps) {
+            guard_ok = false;
+            break;
+        }
+        --sp;
+        const int32_t node = stk[sp];
+        __syncwarp();
+        const NodeBox b = a.nodes[node];
+        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
+        if (start == end) continue;
+        int cls = 0;
+        if (active && end > taken_below) cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
+        const unsigned int partial = __ballot_sync(0xffffffffu, cls == 1);
+        const unsigned int whole = __ballot_sync(0xffffffffu, cls == 2);
+        if (!(partial | whole)) continue;
+        const int32_t fc = a.child[node];
+        if (fc >= 0) {
+            if (whole) {
+                // step 1a: the node lies inside these lanes' kernels; emit its range
+                if (FILL) {
+                    unsigned int todo = whole;
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int64_t o = __shfl_sync(0xffffffffu, out, src);
+                        const int64_t e = __shfl_sync(0xffffffffu, out_end, src);
+                        if (o + (end - start) > e) {
+                            guard_ok = false;
+                            continue;
+                        }
+                        for (uint32_t j = start + lane; j < end; j += 32)
+                            a.cols[o + (j - start)] = static_cast<int32_t>(a.perm[j]);
+                    }
+                }
+                if (cls == 2) {
+                    count += end - start;
+                    out += end - start;
+                    taken_below = end;
+                }
+            }
+            if (partial) {
+                if (sp + 8 <= kStackDepth) {
+                    if (lane < 8) stk[sp + 7 - lane] = fc + static_cast<int32_t>(lane);
+                    sp += 8;
+                    __syncwarp();
+                } else {
+                    guard_ok = false;
+                }
+            }
+        } else {
+            // a leaf: every lane tests every point against its own centre
+            const bool need = cls != 0;
+            for (uint32_t base = start; base < end; base += 32) {
+                const uint32_t m = min(32u, end - base);
+                uint32_t hits = 0;
+#pragma unroll 4
+                for (uint32_t t = 0; t < m; ++t) {
+                    const float4 p = __ldg(&a.pts[base + t]);
+                    const bool in = kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z),
+                                                       a.r, a.r2);
+                    hits |= static_cast<uint32_t>(in) << t;
+                }
+                if (!need) hits = 0;
+                if (FILL) {
+                    const int32_t my_id = lane < m ? static_cast<int32_t>(a.perm[base + lane]) : 0;
+                    unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const uint32_t h = __shfl_sync(0xffffffffu, hits, src);
+                        const int64_t o = __shfl_sync(0xffffffffu, out, src);
+                        const int64_t e = __shfl_sync(0xffffffffu, out_end, src);
+                        if ((h >> lane) & 1u) {
+                            const int64_t pos = o + __popc(h & below);
+                            if (pos < e) a.cols[pos] = my_id;
+                            else guard_ok = false;
+                        }
+                    }
+                    out += __popc(hits);
+                }
+                count += __popc(hits);
+            }
+        }
+    }
+    if (!FILL && active) a.counts[row] = count;
+    if (!guard_ok) atomicOr(a.err, kGuardTripped);
+}
+
+// One centre per thread, its own depth-first walk; points through the permutation.
+template <int KERN, bool FILL>
+__global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
+    const int64_t qi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (qi >= a.nq) return;
+    const float4 c = a.q[qi];
+    const uint32_t row = __float_as_uint(c.w);
+    const bool prune = a.prune != 0;
+    int32_t stk[kStackDepth];
+    int sp = 1;
+    stk[0] = 0;
+    uint32_t count = 0;
+    int64_t out = FILL ? a.row_ptr[row] : 0;
+    const int64_t out_end = FILL ? a.row_ptr[row + 1] : 0;
+    bool guard_ok = true;
+    for (int64_t steps = 0; sp > 0; ++steps) {
+        if (steps >= a.max_steps) {
+            guard_ok = false;
+            break;
+        }
+        const int32_t node = stk[--sp];
+        const NodeBox b = a.nodes[node];
+        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
+        if (start == end) continue;
+        const int cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
+        if (cls == 0) continue;
+        const int32_t fc = a.child[node];
+        if (fc >= 0) {
+            if (cls == 2) {
+                if (FILL) {
+                    if (out + (end - start) > out_end) {
+                        guard_ok = false;
+                        break;
+                    }
+                    for (uint32_t j = start; j < end; ++j) a.cols[out++] = static_cast<int32_t>(a.perm[j]);
+                }
+                count += end - start;
+                continue;
+            }
+            if (sp + 8 <= kStackDepth) {
+                for (int k = 7; k >= 0; --k) stk[sp++] = fc + k;
+            } else {
+                guard_ok = false;
+            }
+        } else {
+            for (uint32_t j = start; j < end; ++j) {
+                const uint32_t id = a.perm[j];
+                const float4 p = a.pts[id];
+                if (kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z), a.r, a.r2)) {
+                    if (FILL) {
+                        if (out < out_end) a.cols[out++] = static_cast<int32_t>(id);
+                        else guard_ok = false;
+                    }
+                    ++count;
+                }
+            }
+        }
+    }
+    if (!FILL) a.counts[row] = count;
+    if (!guard_ok) atomicOr(a.err, kGuardTripped);
+}
+
+template <bool FILL>
+static sfc_status launch_search(const Octree* t, RadiusArgs& a, int kern, cudaStream_t s) {
+    if (a.nq == 0) return SFC_OK;
+    const char* name = FILL ? "radius_fill" : "radius_count";
+    if (t->enc == SFC_ENC_NONE) {
+        const unsigned int grid = grid_for(a.nq, 128);
+        switch (kern) {
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SPHERE, FILL>), grid, 128, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CIRCLE, FILL>), grid, 128, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CUBE, FILL>), grid, 128, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SQUARE, FILL>), grid, 128, 0, a); break;
+        }
+    } else {
+        const int64_t groups = (a.nq + 31) / 32;
+        const unsigned int grid = grid_for(groups, kRadiusWarps);
+        switch (kern) {
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
+        }
+    }
+    return SFC_OK;
+}
+
+static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, float r) {
+    RadiusArgs a;
+    a.pts = t->pts;
+    a.perm = t->perm;
+    a.nodes = t->nodes;
+    a.child = t->child;
+    a.q = q4;
+    a.nq = rows;
+    a.r = r;
+    a.r2 = r * r;  // binary32 product, rounded to nearest
+    a.prune = t->prune;
+    a.counts = nullptr;
+    a.row_ptr = nullptr;
+    a.cols = nullptr;
+    a.err = &t->scal->bad;
+    a.max_steps = t->n_nodes;
+    return a;
+}
+
+// rows = number of output rows; validates the arguments common to the radius calls
+static sfc_status check_radius_args(sfc_octree h, const float* queries, int64_t nq, float r, sfc_kernel kern,
+                                    int64_t* rows) {
+    if (!h) return SFC_ERR_INVALID;
+    if (kern != SFC_SPHERE && kern != SFC_CIRCLE && kern != SFC_CUBE && kern != SFC_SQUARE) return SFC_ERR_INVALID;
+    if (isnan(r)) return SFC_ERR_INVALID;
+    if (!queries) {
+        if (nq != 0 && nq != h->tree.n) return SFC_ERR_INVALID;
+        *rows = h->tree.n;
+        return SFC_OK;
+    }
+    if (nq < 0) return SFC_ERR_INVALID;
+    if (nq > 0x7fffffffLL - 1) return SFC_ERR_TOO_LARGE;
+    if (nq > 0 && !is_device_ptr(queries)) return SFC_ERR_NOT_DEVICE_PTR;
+    *rows = nq;
+    return SFC_OK;
+}
+
+static sfc_status count_impl(const Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
+                             Scratch& scratch, int64_t* row_ptr, const unsigned int* bad, int64_t* nnz) {
+    if (!(r > 0.f) || rows == 0 || t->n == 0) {
+        SFC_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (rows + 1), s));
+    } else {
+        uint32_t* counts = nullptr;
+        SFC_TRY(scratch.alloc(&counts, rows));
+        RadiusArgs a = make_args(t, q4, rows, r);
+        a.counts = counts;
+        SFC_TRY(launch_search<false>(t, a, kern, s));
+        SFC_TRY(scan_u32_to_i64(counts, row_ptr, rows, s, scratch));
+    }
+    unsigned int hbad = 0, herr = 0;
+    SFC_CUDA(cudaMemcpyAsync(nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (bad) SFC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return SFC_ERR_NOT_FINITE;
+    if (herr & kGuardTripped) return SFC_ERR_INTERNAL;
+    return SFC_OK;
+}
+
+static sfc_status fill_impl(const Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
+                            const int64_t* row_ptr, int32_t* cols) {
+    if (!(r > 0.f) || rows == 0 || t->n == 0) return SFC_OK;
+    RadiusArgs a = make_args(t, q4, rows, r);
+    a.row_ptr = row_ptr;
+    a.cols = cols;
+    return launch_search<true>(t, a, kern, s);
+}
+
+static sfc_status check_guard(const Octree* t, cudaStream_t s) {
+    unsigned int herr = 0;
+    SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    return (herr & kGuardTripped) ? SFC_ERR_INTERNAL : SFC_OK;
+}
+
+static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, cudaStream_t s, Scratch& scratch,
+                          const float4** q4, unsigned int** bad) {
+    *bad = nullptr;
+    if (queries) {
+        SFC_TRY(scratch.alloc(bad, 1));
+        SFC_CUDA(cudaMemsetAsync(*bad, 0, sizeof(unsigned int), s));
+    }
+    return prepare_queries(t, queries, rows, s, scratch, q4, *bad);
+}
+
+}  // namespace sfc
+
+using sfc::Octree;
+
+extern "C" {
+
+sfc_status radius_count(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                        void* cuda_stream, int64_t* row_ptr, int64_t* nnz) {
+    int64_t rows = 0;
+    SFC_TRY(sfc::check_radius_args(h, queries_xyz, n_queries, r, kern, &rows));
+    if (!row_ptr || !nnz) return SFC_ERR_INVALID;
+    if (!sfc::is_device_ptr(row_ptr)) return SFC_ERR_NOT_DEVICE_PTR;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc::Scratch scratch(s);
+    const float4* q4 = nullptr;
+    unsigned int* bad = nullptr;
+    SFC_TRY(sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad));
+    return sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, nnz);
+}
+
+sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                       void* cuda_stream, const int64_t* row_ptr, int32_t* cols) {
+    int64_t rows = 0;
+    SFC_TRY(sfc::check_radius_args(h, queries_xyz, n_queries, r, kern, &rows));
+    if (!row_ptr || !cols) return SFC_ERR_INVALID;
+    if (!sfc::is_device_ptr(row_ptr) || !sfc::is_device_ptr(cols)) return SFC_ERR_NOT_DEVICE_PTR;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc::Scratch scratch(s);
+    const float4* q4 = nullptr;
+    unsigned int* bad = nullptr;
+    SFC_TRY(sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad));
+    return sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols);
+}
+
+sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                         void* cuda_stream, sfc_csr* out) {
+    if (!out) return SFC_ERR_INVALID;
+    out->n_rows = 0;
+    out->nnz = 0;
+    out->row_ptr = nullptr;
+    out->cols = nullptr;
+    int64_t rows = 0;
+    SFC_TRY(sfc::check_radius_args(h, queries_xyz, n_queries, r, kern, &rows));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc_status st;
+    int64_t nnz = 0;
+    int64_t* row_ptr = nullptr;
+    int32_t* cols = nullptr;
+    {
+        sfc::Scratch scratch(s);
+        const float4* q4 = nullptr;
+        unsigned int* bad = nullptr;
+        st = sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad);
+        if (st == SFC_OK) st = sfc::dev_alloc(&row_ptr, rows + 1, s);
+        if (st == SFC_OK) st = sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, &nnz);
+        if (st == SFC_OK) st = sfc::dev_alloc(&cols, nnz, s);
+        if (st == SFC_OK) st = sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols);
+        if (st == SFC_OK) st = sfc::check_guard(&h->tree, s);
+    }
+    if (st != SFC_OK) {
+        sfc::dev_free(row_ptr, s);
+        sfc::dev_free(cols, s);
+        return st;
+    }
+    out->n_rows = rows;
+    out->nnz = nnz;
+    out->row_ptr = row_ptr;
+    out->cols = cols;
+    return SFC_OK;
+}
+
+sfc_status sfc_csr_free(sfc_csr* csr, void* cuda_stream) {
+    if (!csr) return SFC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc::dev_free(csr->row_ptr, s);
+    sfc::dev_free(csr->cols, s);
+    csr->row_ptr = nullptr;
+    csr->cols = nullptr;
+    csr->n_rows = 0;
+    csr->nnz = 0;
+    return SFC_OK;
+}
+
+}  // extern "C"
