@@ -1,0 +1,396 @@
+"""Benchmark of the SFC linear-octree neighbour search on one GB300 per rank.
+
+One step = the whole path over one synthetic 10M-point LiDAR-like tile already resident
+in HBM: octree_build (bounding box, Hilbert codes, radix sort, gather, linear octree),
+an all-points sphere search with r = 2 m (count, scan, fill) and an all-points kNN
+search with k = 16.  value = queries answered per second (10M radius + 10M kNN queries
+per step).  With --gpus N (launched by torchrun) every rank runs its own replica of the
+workload (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "lidar_tile_10M",
+    "description": "synthetic aerial LiDAR-like tile, 1 km x 1 km, 10 pts/m^2 (60% ground, 30% vegetation, "
+                   "10% buildings, 3 cm jitter)",
+    "points": 10_000_000,
+    "encoding": "hilbert",
+    "leaf_capacity": 32,
+    "radius": {"kernel": "sphere", "r": 2.0},
+    "knn_k": 16,
+}
+METRIC = "radius/kNN queries/s on 1 GB300 (all-points sphere r=2 m + kNN k=16 over a fresh octree per step)"
+UNIT = "queries/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
+# with the sha256 of the source file it was measured on (null once the source changes).
+NCU_TRAFFIC = {}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--points", type=int, default=WORKLOAD["points"], help="override the cloud size (testing)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def aggregate(step_ms_total: float, units: float, world: int, device=None):
+    """Max of the timed region over ranks and the sum of the units processed."""
+    import torch
+    import torch.distributed as dist
+
+    if world == 1:
+        return step_ms_total, units
+    t = torch.tensor([step_ms_total], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str | None = None):
+        self.gpu = gpu_index
+        self.path = path
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        if self.path:
+            with open(self.path, "w") as f:
+                f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- the step
+def run_step(sfc, pts, cfg):
+    """The whole path once; returns (tree, row_ptr, cols, nnz, idx, d2)."""
+    tree = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
+    row_ptr, nnz = sfc.radius_count(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
+    cols = sfc.radius_fill(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"], row_ptr, nnz)
+    idx, d2 = sfc.knn(tree, None, cfg["knn_k"])
+    return tree, row_ptr, cols, nnz, idx, d2
+
+
+def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
+    """Bytes one launch of ``kernel`` must move at minimum (the per-unit figures of the design doc)."""
+    table = {
+        "radius_fill": 16 * n + 8 * (n + 1) + 4 * nnz,   # points + ids, row pointers, neighbour ids
+        "radius_count": 12 * n + 4 * n,                  # points, counts
+        "knn": 16 * n + 8 * n * k,                       # points + ids, k (id, d2) pairs per centre
+        "radix_scatter": 24 * n,                         # read + write (code, index)
+        "radix_histogram": 8 * n,
+        "encode": 12 * n + 12 * n,
+        "gather_points": 16 * n + 16 * n,
+        "bbox": 12 * n,
+    }
+    return table.get(kernel)
+
+
+def source_sha(name: str) -> str:
+    with open(os.path.join(ROOT, "paper_2603_06771_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def load_peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def time_oracle(xyz: np.ndarray, cfg: dict, sample: int, seed: int, build_s: float | None = None):
+    """Oracle timing: a full build (section 4 + 5.1 + pointer octree) unless build_s is
+    given, then radius + kNN on a seeded sample of centres; returns seconds."""
+    import oracle
+
+    enc = oracle.ENCODINGS[cfg["encoding"]]
+    if build_s is None:
+        t0 = time.perf_counter()
+        pipe = oracle.Pipeline(xyz, enc, cfg["leaf_capacity"])
+        build_s = time.perf_counter() - t0
+    else:
+        pipe = time_oracle.pipe
+    time_oracle.pipe = pipe
+    rows = np.sort(np.random.default_rng(seed).choice(len(xyz), sample, replace=False))
+    q = xyz[rows]
+    t0 = time.perf_counter()
+    pipe.tree.radius(q, cfg["radius"]["r"], oracle.KERNELS[cfg["radius"]["kernel"]])
+    radius_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pipe.tree.knn(q, cfg["knn_k"])
+    knn_s = time.perf_counter() - t0
+    return build_s, radius_s, knn_s
+
+
+def cpu_step_estimate(n: int, sample: int, build_s: float, radius_s: float, knn_s: float) -> float:
+    """Seconds of one full step on the CPU: the build plus the sampled searches scaled to n centres."""
+    return build_s + (radius_s + knn_s) * n / sample
+
+
+def reference_arm(args, cfg):
+    import oracle
+    import synth
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.points
+    xyz = synth.lidar_tile(n, synth.CONFIG_SEED[2]) if n != WORKLOAD["points"] else synth.config_cloud(2)
+    cores = oracle.num_cpus()
+    sample = max(1, min(n, 4000))
+    build_s, _, _ = time_oracle(xyz, cfg, sample, 0)          # the build, timed once
+    for w in range(args.warmup):
+        time_oracle(xyz, cfg, sample, 1000 + w, build_s)
+    steps = []
+    for s in range(args.steps):
+        _, rs, ks = time_oracle(xyz, cfg, sample, s, build_s)
+        steps.append(cpu_step_estimate(n, sample, build_s, rs, ks))
+    step_s = statistics.mean(steps)
+    value = 2 * n / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(cfg, points=n),
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
+                         "sample": (f"oracle (plain C pointer octree, {cores} threads for searches, 1 thread for "
+                                    f"the build) on the same {n}-point cloud: full build timed once "
+                                    f"({build_s:.2f} s); each step times sphere r=2 and kNN k=16 on {sample} "
+                                    f"seeded centres and scales them to all {n} centres")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main(argv=None):
+    args = parse_args(argv)
+    cfg = dict(WORKLOAD)
+    if args.impl == "reference":
+        return reference_arm(args, cfg)
+
+    import torch
+
+    import paper_2603_06771_gb300 as sfc
+    import synth
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    sfc.build()
+    n = args.points
+    seed = synth.CONFIG_SEED[2] + rank
+    xyz = synth.config_cloud(2) if (n == WORKLOAD["points"] and rank == 0) else synth.lidar_tile(n, seed)
+    pts = torch.from_numpy(xyz).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    k = cfg["knn_k"]
+
+    # warm-up (also sizes the outputs)
+    nnz = 0
+    for _ in range(args.warmup):
+        tree, row_ptr, cols, nnz, idx, d2 = run_step(sfc, pts, cfg)
+        tree.free()
+        del row_ptr, cols, idx, d2
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each, CUDA events around each step
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = sfc.launch_count()
+    sfc.profile_enable(True)
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s)
+        starts[s].record(stream)
+        tree, row_ptr, cols, nnz, idx, d2 = run_step(sfc, pts, cfg)
+        ends[s].record(stream)
+        tree.free()
+        del row_ptr, cols, idx, d2
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - wall0
+    sfc.profile_enable(False)
+    launches = sfc.launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    prof = sfc.profile_read()
+    total_ms, units = aggregate(sum(step_ms), 2.0 * n * args.steps, world, torch.device("cuda", local))
+    ms_per_step = total_ms / args.steps
+    value = units / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    peak, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    dom_avg_ms = dom_ms / dom_launches
+    alg = algorithmic_bytes(dom_name, n, nnz, k)
+    roof = None
+    if alg is not None:
+        achieved = alg / (dom_avg_ms / 1e3) / 1e9
+        src = {"radius_fill": "sfc_radius.cu", "radius_count": "sfc_radius.cu", "knn": "sfc_knn.cu"}.get(
+            dom_name, "sfc_runtime.cu")
+        rec = NCU_TRAFFIC.get(dom_name)
+        traffic = rec["bytes_per_launch"] if rec and rec.get("sha256") == source_sha(src) else None
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s", "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_avg_ms}
+    kernels = {name: {"launches": c, "total_ms": ms, "share": ms / sum(step_ms)} for name, (c, ms) in
+               sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end through the public API: pinned host points in, every result back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        h_xyz = torch.from_numpy(xyz).pin_memory()
+        h_rp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+        h_cols = torch.empty(int(nnz * 1.05) + 1024, dtype=torch.int32, pin_memory=True)
+        h_idx = torch.empty((n, k), dtype=torch.int32, pin_memory=True)
+        h_d2 = torch.empty((n, k), dtype=torch.float32, pin_memory=True)
+        d_pts = torch.empty_like(pts)
+        e_ms = []
+        for s in range(args.warmup + args.steps):
+            flush.fill_(s)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            d_pts.copy_(h_xyz, non_blocking=True)
+            tree, row_ptr, cols, e_nnz, idx, d2 = run_step(sfc, d_pts, cfg)
+            h_rp.copy_(row_ptr, non_blocking=True)
+            h_cols[:e_nnz].copy_(cols, non_blocking=True)
+            h_idx.copy_(idx, non_blocking=True)
+            h_d2.copy_(d2, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            tree.free()
+            del row_ptr, cols, idx, d2
+            if s >= args.warmup:
+                e_ms.append(a.elapsed_time(b))
+        e_total, e_units = aggregate(sum(e_ms), 2.0 * n * args.steps, world, torch.device("cuda", local))
+        e2e = {"value": e_units / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
+               "d2h_bytes_per_step": 8 * (n + 1) + 4 * nnz + 8 * n * k, "ms_per_step": e_total / args.steps}
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:
+        import oracle
+
+        sample = min(n, 20000)
+        b_s, r_s, k_s = time_oracle(xyz, cfg, sample, 7)
+        est = cpu_step_estimate(n, sample, b_s, r_s, k_s)
+        cpu = {"value": 2 * n / est, "unit": UNIT, "cores": oracle.num_cpus(), "kind": "oracle",
+               "sample": (f"full oracle build of the {n}-point cloud ({b_s:.2f} s, 1 thread) + sphere r=2 "
+                          f"({r_s:.3f} s) and kNN k=16 ({k_s:.3f} s) for {sample} seeded centres on "
+                          f"{oracle.num_cpus()} threads, scaled to {n} centres")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(cfg, points=n, l2="flushed before every timed step (512 MiB write)",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "nnz": nnz, "mu": nnz / n, "neighbours_per_s": nnz * args.steps * world / (total_ms / 1e3),
+            "gpu_launches": launches, "wall_s": wall_s, "roofline": roof, "kernels": kernels,
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
