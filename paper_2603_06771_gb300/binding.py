@@ -24,7 +24,8 @@ KERNELS = {"sphere": 0, "circle": 1, "cube": 2, "square": 3}
 
 SFC_OK = 0
 STATUS_NAMES = {0: "SFC_OK", 1: "SFC_ERR_INVALID", 2: "SFC_ERR_OOM", 3: "SFC_ERR_CUDA", 4: "SFC_ERR_TIMEOUT",
-                5: "SFC_ERR_TOO_LARGE", 6: "SFC_ERR_NOT_DEVICE_PTR", 7: "SFC_ERR_NOT_FINITE"}
+                5: "SFC_ERR_TOO_LARGE", 6: "SFC_ERR_NOT_DEVICE_PTR", 7: "SFC_ERR_NOT_FINITE",
+                8: "SFC_ERR_INTERNAL"}
 
 
 class SFCError(RuntimeError):

@@ -38,7 +38,7 @@ def test_binding_covers_the_abi():
 
 def test_status_strings():
     lib = binding.lib()
-    for code in range(8):
+    for code in range(9):
         assert lib.sfc_status_string(code)
     assert lib.sfc_launch_count() >= 0
 
