@@ -137,6 +137,25 @@ sfc_status radius_count(sfc_octree h, const float* queries_xyz, int64_t n_querie
 sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
                        void* cuda_stream, const int64_t* row_ptr, int32_t* cols);
 
+/* radius_count for every point of the tree (queries_xyz == NULL) without allocating any
+ * device memory.  The paper has no counterpart: this exists for callers that cannot let a
+ * library allocate, such as an application that reserves its whole device memory budget
+ * up front (an allocation inside the call could fail or disturb its pool) or a loop with a
+ * hard latency budget.  The per-point counts and scan sums live in a file-scope __device__
+ * array of the library (about 8 MiB, held by every GPU that loads the library until the
+ * process exits) instead of device scratch.
+ *   row_ptr  device, n_points + 1 int64, caller-owned; *nnz (host) receives the total.
+ *   Same results as radius_count(h, NULL, 0, r, kern, ...).
+ * Limits: at most radius_count_static_max_points() points (2^21), else SFC_ERR_TOO_LARGE.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call uses the same array and it
+ * keeps the last call's contents, so calls that overlap on the GPU race with each other.
+ * Synchronises cuda_stream once (to read nnz). */
+sfc_status radius_count_static(sfc_octree h, float r, sfc_kernel kern, void* cuda_stream, int64_t* row_ptr,
+                               int64_t* nnz);
+/* The largest point count radius_count_static accepts. */
+int64_t radius_count_static_max_points(void);
+
 /* Free a CSR allocated by radius_search (stream ordered); zeroes *csr. */
 sfc_status sfc_csr_free(sfc_csr* csr, void* cuda_stream);
 

@@ -121,6 +121,13 @@ void dev_free(void* p, cudaStream_t s);
 // in and out may alias (in-place) when they have the same type.
 sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
 sfc_status scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
+// The same scan with the per-tile sums in a caller buffer of scan_tile_count(n) entries.
+int64_t scan_tile_count(int64_t n);
+sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s);
+// All-points count pass of the radius search into caller buffers (counts: one entry per
+// point, tile_sums: scan_tile_count(n) entries); reads nnz back (one synchronisation).
+sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_t s, uint32_t* counts,
+                                 int64_t* tile_sums, int64_t* row_ptr, int64_t* nnz);
 
 // Stable LSD radix sort of (key, value) pairs by the low 63 bits of key; the result ends
 // in keys / vals, keys_alt / vals_alt are work buffers of the same size.

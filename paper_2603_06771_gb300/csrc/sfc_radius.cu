@@ -317,6 +317,24 @@ static sfc_status count_impl(const Octree* t, const float4* q4, int64_t rows, fl
     return SFC_OK;
 }
 
+sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_t s, uint32_t* counts,
+                                 int64_t* tile_sums, int64_t* row_ptr, int64_t* nnz) {
+    const int64_t rows = t->n;
+    if (!(r > 0.f) || rows == 0) {
+        SFC_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (rows + 1), s));
+    } else {
+        RadiusArgs a = make_args(t, t->pts, rows, r);
+        a.counts = counts;
+        SFC_TRY(launch_search<false>(t, a, kern, s));
+        SFC_TRY(scan_u32_to_i64_presized(counts, row_ptr, rows, tile_sums, s));
+    }
+    unsigned int herr = 0;
+    SFC_CUDA(cudaMemcpyAsync(nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    return (herr & kGuardTripped) ? SFC_ERR_INTERNAL : SFC_OK;
+}
+
 static sfc_status fill_impl(const Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
                             const int64_t* row_ptr, int32_t* cols) {
     if (!(r > 0.f) || rows == 0 || t->n == 0) return SFC_OK;

@@ -219,6 +219,22 @@ sfc_status scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStr
     return scan_impl<uint32_t, uint32_t>(in, out, n, s, scratch);
 }
 
+int64_t scan_tile_count(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s) {
+    if (n == 0) {
+        SFC_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return SFC_OK;
+    }
+    const int64_t tiles = scan_tile_count(n);
+    SFC_LAUNCH("scan_tile_sums", s, (k_scan_tile_sums<uint32_t, int64_t>), static_cast<unsigned int>(tiles),
+               kScanThreads, 0, in, n, tile_sums);
+    SFC_LAUNCH("scan_spine", s, k_scan_spine<int64_t>, 1, 1024, 0, tile_sums, tiles);
+    SFC_LAUNCH("scan_apply", s, (k_scan_apply<uint32_t, int64_t>), static_cast<unsigned int>(tiles), kScanThreads,
+               0, in, out, n, tile_sums);
+    return SFC_OK;
+}
+
 // ---------------------------------------------------------------------------------
 // LSD radix sort of (63-bit code, uint32 index) pairs, 8-bit digits, 8 passes.
 // Per pass: per-tile digit histograms (digit-major, so one exclusive scan gives every
