@@ -52,6 +52,11 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--points", type=int, default=WORKLOAD["points"], help="override the cloud size (testing)")
+    ap.add_argument("--leaf-capacity", type=int, default=WORKLOAD["leaf_capacity"])
+    ap.add_argument("--encoding", choices=["none", "morton", "hilbert"], default=WORKLOAD["encoding"])
+    ap.add_argument("--radius", type=float, default=WORKLOAD["radius"]["r"])
+    ap.add_argument("--kernel", choices=["sphere", "circle", "cube", "square"], default=WORKLOAD["radius"]["kernel"])
+    ap.add_argument("--k", type=int, default=WORKLOAD["knn_k"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -246,7 +251,8 @@ def reference_arm(args, cfg):
 # ----------------------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
-    cfg = dict(WORKLOAD)
+    cfg = dict(WORKLOAD, leaf_capacity=args.leaf_capacity, encoding=args.encoding, knn_k=args.k,
+               radius={"kernel": args.kernel, "r": args.radius})
     if args.impl == "reference":
         return reference_arm(args, cfg)
 

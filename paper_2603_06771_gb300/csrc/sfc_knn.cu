@@ -35,6 +35,7 @@ struct KnnArgs {
     float* out_d2;
     unsigned int* err;
     int64_t max_steps;
+    int64_t window;   // > 0: seed each warp's lists from this many curve neighbours on each side
 };
 
 __device__ __forceinline__ float box_lower_bound(const NodeBox& b, float cx, float cy, float cz) {
@@ -46,63 +47,108 @@ __device__ __forceinline__ bool pair_less(float da, uint32_t ia, float db, uint3
     return da < db || (da == db && ia < ib);
 }
 
-// Sorted list of the KMAX best pairs; insert keeps it sorted and drops the largest.
+// A (d2, index) pair packed so that unsigned order is pair order: d2 is never negative
+// (a sum of rounded squares), and the bits of a non-negative float order like its value.
+__device__ __forceinline__ uint64_t pair_key(float d, uint32_t id) {
+    return (static_cast<uint64_t>(__float_as_uint(d)) << 32) | id;
+}
+constexpr uint64_t kNoPair = (static_cast<uint64_t>(0x7f800000u) << 32) | kNoIndex;  // (+inf, no index)
+
+// The KMAX best pairs of one centre, sorted ascending in registers; the k-th (k <= KMAX)
+// is the pruning bound.  insert() decides every slot independently from the comparisons
+// "slot s stays before the new pair" (true for a prefix of the sorted list): slot s keeps
+// its pair, takes the new one, or takes slot s-1's, and the last pair drops off.
 template <int KMAX>
 struct BestList {
-    float d[KMAX];
-    uint32_t i[KMAX];
+    uint64_t key[KMAX];
+    uint64_t kth;  // the k-th pair
     __device__ __forceinline__ void init() {
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            d[s] = INFINITY;
-            i[s] = kNoIndex;
+        for (int s = 0; s < KMAX; ++s) key[s] = kNoPair;
+        kth = kNoPair;
+    }
+    __device__ __forceinline__ void insert(uint64_t nk, int k) {
+        bool stays[KMAX];
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) stays[s] = key[s] < nk;
+#pragma unroll
+        for (int s = KMAX - 1; s > 0; --s) key[s] = stays[s] ? key[s] : (stays[s - 1] ? nk : key[s - 1]);
+        key[0] = stays[0] ? key[0] : nk;
+        if (k == KMAX) {
+            kth = key[KMAX - 1];
+        } else {
+            kth = key[0];
+#pragma unroll
+            for (int s = 1; s < KMAX; ++s)
+                if (s == k - 1) kth = key[s];
         }
     }
-    __device__ __forceinline__ void insert(float nd, uint32_t ni) {
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            const bool before = pair_less(nd, ni, d[s], i[s]);
-            const float td = d[s];
-            const uint32_t ti = i[s];
-            d[s] = before ? nd : td;
-            i[s] = before ? ni : ti;
-            nd = before ? td : nd;
-            ni = before ? ti : ni;
-        }
-    }
-    // the k-th best pair (k <= KMAX)
-    __device__ __forceinline__ void kth(int k, float* kd, uint32_t* ki) const {
-        float rd = d[0];
-        uint32_t ri = i[0];
-#pragma unroll
-        for (int s = 1; s < KMAX; ++s)
-            if (s == k - 1) {
-                rd = d[s];
-                ri = i[s];
-            }
-        *kd = rd;
-        *ki = ri;
-    }
+    __device__ __forceinline__ float kth_d2() const { return __uint_as_float(static_cast<uint32_t>(kth >> 32)); }
     __device__ __forceinline__ void store(const KnnArgs& a, uint32_t row) const {
         const int64_t base = static_cast<int64_t>(row) * a.k;
 #pragma unroll
         for (int s = 0; s < KMAX; ++s)
             if (s < a.k) {
-                a.out_idx[base + s] = i[s] == kNoIndex ? -1 : static_cast<int32_t>(i[s]);
-                a.out_d2[base + s] = d[s];
+                const uint32_t id = static_cast<uint32_t>(key[s]);
+                a.out_idx[base + s] = id == kNoIndex ? -1 : static_cast<int32_t>(id);
+                a.out_d2[base + s] = __uint_as_float(static_cast<uint32_t>(key[s] >> 32));
             }
     }
 };
 
-// children order key: empty children last, then by bound, then by child number
+// Test the points at sorted positions [lo, hi) against every lane's centre and insert the
+// better ones: pass 1 marks, per 32-point chunk, the points that beat the lane's current
+// k-th pair; pass 2 lets each lane insert its marked points.
+template <int KMAX>
+__device__ __forceinline__ void scan_points(const KnnArgs& a, uint32_t lo, uint32_t hi, const float4& c, bool need,
+                                            BestList<KMAX>& best) {
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t m = min(32u, hi - base);
+        uint32_t cand = 0;
+#pragma unroll 4
+        for (uint32_t t = 0; t < m; ++t) {
+            const float4 p = __ldg(&a.pts[base + t]);
+            const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
+            if (pair_key(d, __float_as_uint(p.w)) < best.kth) cand |= 1u << t;
+        }
+        if (!need) cand = 0;
+        while (__ballot_sync(0xffffffffu, cand != 0)) {
+            if (cand) {
+                const int t = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const float4 p = __ldg(&a.pts[base + t]);
+                const uint64_t nk =
+                    pair_key(sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z)), __float_as_uint(p.w));
+                if (nk < best.kth) best.insert(nk, a.k);
+            }
+        }
+    }
+}
+
+// children order key: empty or unreachable children last, then by bound, then by number
 __device__ __forceinline__ uint64_t child_order_key(const NodeBox& cb, float gx, float gy, float gz, int ci) {
     const bool empty = __float_as_uint(cb.lo.w) == __float_as_uint(cb.hi.w);
     const uint32_t bound = empty ? 0xffffffffu : float_to_ordered(box_lower_bound(cb, gx, gy, gz));
     return (static_cast<uint64_t>(bound) << 32) | static_cast<uint32_t>(ci);
 }
 
+// Squared distance bound between a node box and the box of a group of centres; no
+// centre of the group is nearer to any point of the node (rounding is monotone).
+__device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, float gly, float glz, float ghx,
+                                                   float ghy, float ghz) {
+    return sq_dist(fmaxf(fmaxf(__fsub_rn(b.lo.x, ghx), __fsub_rn(glx, b.hi.x)), 0.0f),
+                   fmaxf(fmaxf(__fsub_rn(b.lo.y, ghy), __fsub_rn(gly, b.hi.y)), 0.0f),
+                   fmaxf(fmaxf(__fsub_rn(b.lo.z, ghz), __fsub_rn(glz, b.hi.z)), 0.0f));
+}
+
+// resident blocks per SM the register budget is sized for (4 warps each)
 template <int KMAX>
-__global__ void __launch_bounds__(kKnnWarps * 32) k_knn_group(KnnArgs a) {
+struct KnnOccupancy {
+    static constexpr int kBlocks = KMAX <= 8 ? 8 : (KMAX <= 16 ? 5 : (KMAX <= 32 ? 3 : 2));
+};
+
+template <int KMAX>
+__global__ void __launch_bounds__(kKnnWarps * 32, KnnOccupancy<KMAX>::kBlocks) k_knn_group(KnnArgs a) {
     __shared__ int32_t stack[kKnnWarps][kStackDepth];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
@@ -114,22 +160,40 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_group(KnnArgs a) {
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t row = __float_as_uint(c.w);
 
-    // centre of the group, used only to order the walk
+    // centre (orders the walk) and bounding box (prunes it) of the group's centres
     const unsigned int act = __ballot_sync(0xffffffffu, active);
     const float inv = 1.0f / static_cast<float>(__popc(act));
     float gx = active ? c.x : 0.f, gy = active ? c.y : 0.f, gz = active ? c.z : 0.f;
+    float glx = active ? c.x : INFINITY, gly = active ? c.y : INFINITY, glz = active ? c.z : INFINITY;
+    float ghx = active ? c.x : -INFINITY, ghy = active ? c.y : -INFINITY, ghz = active ? c.z : -INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         gx += __shfl_xor_sync(0xffffffffu, gx, o);
         gy += __shfl_xor_sync(0xffffffffu, gy, o);
         gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        glx = fminf(glx, __shfl_xor_sync(0xffffffffu, glx, o));
+        gly = fminf(gly, __shfl_xor_sync(0xffffffffu, gly, o));
+        glz = fminf(glz, __shfl_xor_sync(0xffffffffu, glz, o));
+        ghx = fmaxf(ghx, __shfl_xor_sync(0xffffffffu, ghx, o));
+        ghy = fmaxf(ghy, __shfl_xor_sync(0xffffffffu, ghy, o));
+        ghz = fmaxf(ghz, __shfl_xor_sync(0xffffffffu, ghz, o));
     }
     gx *= inv; gy *= inv; gz *= inv;
 
     BestList<KMAX> best;
     best.init();
-    float kd = INFINITY;
-    uint32_t ki = kNoIndex;
+
+    // All-points search on a cloud ordered along the curve: the centres are the points
+    // at positions first .. first + 31, and their curve neighbours are mostly their space
+    // neighbours.  Seeding every list with the points of a window around those positions
+    // gives a near-final k-th distance before the walk; the walk skips the window.
+    uint32_t win_lo = 0, win_hi = 0;
+    if (a.window > 0) {
+        win_lo = static_cast<uint32_t>(first > a.window ? first - a.window : 0);
+        const int64_t hi = first + 32 + a.window;
+        win_hi = static_cast<uint32_t>(hi < a.nq ? hi : a.nq);
+        scan_points<KMAX>(a, win_lo, win_hi, c, active, best);
+    }
 
     bool guard_ok = true;
     int sp = 1;
@@ -145,14 +209,21 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_group(KnnArgs a) {
         __syncwarp();
         const NodeBox b = a.nodes[node];
         const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
-        if (start == end) continue;
-        const bool need = active && box_lower_bound(b, c.x, c.y, c.z) <= kd;
+        const bool need = active && box_lower_bound(b, c.x, c.y, c.z) <= best.kth_d2();
         if (!__ballot_sync(0xffffffffu, need)) continue;
         const int32_t fc = a.child[node];
         if (fc >= 0) {
-            // order the eight children nearest first (bitonic sort over lanes 0..7)
+            // the largest k-th distance of the group bounds what any lane still needs
+            float mkd = active ? best.kth_d2() : -INFINITY;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mkd = fmaxf(mkd, __shfl_xor_sync(0xffffffffu, mkd, o));
+            // reachable children, nearest to the group centre first (bitonic sort, lanes 0..7)
             uint64_t key = ~0ull;
-            if (lane < 8) key = child_order_key(a.nodes[fc + lane], gx, gy, gz, static_cast<int>(lane));
+            if (lane < 8) {
+                const NodeBox cb = a.nodes[fc + lane];
+                if (group_lower_bound(cb, glx, gly, glz, ghx, ghy, ghz) <= mkd)
+                    key = child_order_key(cb, gx, gy, gz, static_cast<int>(lane));
+            }
 #pragma unroll
             for (int size = 2; size <= 8; size <<= 1) {
 #pragma unroll
@@ -174,15 +245,9 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_group(KnnArgs a) {
             }
             __syncwarp();
         } else {
-            for (uint32_t j = start; j < end; ++j) {
-                const float4 p = __ldg(&a.pts[j]);
-                const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
-                const uint32_t id = __float_as_uint(p.w);
-                if (need && pair_less(d, id, kd, ki)) {
-                    best.insert(d, id);
-                    best.kth(a.k, &kd, &ki);
-                }
-            }
+            // the leaf's points outside the seeding window
+            scan_points<KMAX>(a, start, min(end, win_lo > start ? win_lo : start), c, need, best);
+            scan_points<KMAX>(a, max(start, win_hi), end, c, need, best);
         }
     }
     if (active) best.store(a, row);
@@ -197,8 +262,6 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
     const uint32_t row = __float_as_uint(c.w);
     BestList<KMAX> best;
     best.init();
-    float kd = INFINITY;
-    uint32_t ki = kNoIndex;
     int32_t stk[kStackDepth];
     int sp = 1;
     stk[0] = 0;
@@ -212,7 +275,7 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
         const NodeBox b = a.nodes[node];
         const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
         if (start == end) continue;
-        if (box_lower_bound(b, c.x, c.y, c.z) > kd) continue;
+        if (box_lower_bound(b, c.x, c.y, c.z) > best.kth_d2()) continue;
         const int32_t fc = a.child[node];
         if (fc >= 0) {
             uint64_t keys[8];
@@ -236,11 +299,8 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
             for (uint32_t j = start; j < end; ++j) {
                 const uint32_t id = a.perm[j];
                 const float4 p = a.pts[id];
-                const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
-                if (pair_less(d, id, kd, ki)) {
-                    best.insert(d, id);
-                    best.kth(a.k, &kd, &ki);
-                }
+                const uint64_t nk = pair_key(sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z)), id);
+                if (nk < best.kth) best.insert(nk, a.k);
             }
         }
     }
@@ -311,6 +371,7 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.out_d2 = out_d2;
         a.err = &t->scal->bad;
         a.max_steps = t->n_nodes;
+        a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? 32 : 0;
         if (k <= 8) SFC_TRY(sfc::launch_knn<8>(t, a, s));
         else if (k <= 16) SFC_TRY(sfc::launch_knn<16>(t, a, s));
         else if (k <= 32) SFC_TRY(sfc::launch_knn<32>(t, a, s));

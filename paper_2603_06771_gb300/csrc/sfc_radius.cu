@@ -59,6 +59,14 @@ __device__ __forceinline__ int classify_box(const NodeBox& b, float cx, float cy
     return kernel_holds<KERN>(fx, fy, fz, r, r2) ? 2 : 1;
 }
 
+// Gap between a box and the box [glo, ghi] of a group of centres, per axis (0 when they
+// overlap).  For any centre c in the group box and any point p in the node box,
+// |fl(p - c)| >= gap on that axis (rounding is monotone), so a failed kernel test on the
+// gaps proves that no centre of the group reaches any point of the node.
+__device__ __forceinline__ float axis_gap(float lo, float hi, float glo, float ghi) {
+    return fmaxf(fmaxf(__fsub_rn(lo, ghi), __fsub_rn(glo, hi)), 0.0f);
+}
+
 template <int KERN, bool FILL>
 __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a) {
     __shared__ int32_t stack[kRadiusWarps][kStackDepth];
@@ -79,6 +87,19 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
     uint32_t taken_below = 0;  // positions below this were emitted as a whole range
     bool guard_ok = true;
 
+    // bounding box of the group's centres
+    float glx = active ? c.x : INFINITY, gly = active ? c.y : INFINITY, glz = active ? c.z : INFINITY;
+    float ghx = active ? c.x : -INFINITY, ghy = active ? c.y : -INFINITY, ghz = active ? c.z : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        glx = fminf(glx, __shfl_xor_sync(0xffffffffu, glx, o));
+        gly = fminf(gly, __shfl_xor_sync(0xffffffffu, gly, o));
+        glz = fminf(glz, __shfl_xor_sync(0xffffffffu, glz, o));
+        ghx = fmaxf(ghx, __shfl_xor_sync(0xffffffffu, ghx, o));
+        ghy = fmaxf(ghy, __shfl_xor_sync(0xffffffffu, ghy, o));
+        ghz = fmaxf(ghz, __shfl_xor_sync(0xffffffffu, ghz, o));
+    }
+
     int sp = 1;
     if (lane == 0) stk[0] = 0;
     __syncwarp();
@@ -91,15 +112,13 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
         const int32_t node = stk[sp];
         __syncwarp();
         const NodeBox b = a.nodes[node];
-        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
-        if (start == end) continue;
-        int cls = 0;
-        if (active && end > taken_below) cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
-        const unsigned int partial = __ballot_sync(0xffffffffu, cls == 1);
-        const unsigned int whole = __ballot_sync(0xffffffffu, cls == 2);
-        if (!(partial | whole)) continue;
         const int32_t fc = a.child[node];
+        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
         if (fc >= 0) {
+            int cls = 0;
+            if (active && end > taken_below) cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
+            const unsigned int partial = __ballot_sync(0xffffffffu, cls == 1);
+            const unsigned int whole = __ballot_sync(0xffffffffu, cls == 2);
             if (whole) {
                 // step 1a: the node lies inside these lanes' kernels; emit its range
                 if (FILL) {
@@ -124,17 +143,31 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
                 }
             }
             if (partial) {
-                if (sp + 8 <= kStackDepth) {
-                    if (lane < 8) stk[sp + 7 - lane] = fc + static_cast<int32_t>(lane);
-                    sp += 8;
-                    __syncwarp();
+                // keep the non-empty children that some centre of the group may reach;
+                // the first child ends on top of the stack
+                bool keep = false;
+                if (lane < 8) {
+                    const NodeBox cb = a.nodes[fc + lane];
+                    if (__float_as_uint(cb.lo.w) != __float_as_uint(cb.hi.w))
+                        keep = kernel_holds<KERN>(axis_gap(cb.lo.x, cb.hi.x, glx, ghx),
+                                                  axis_gap(cb.lo.y, cb.hi.y, gly, ghy),
+                                                  axis_gap(cb.lo.z, cb.hi.z, glz, ghz), a.r, a.r2);
+                }
+                const unsigned int kept = __ballot_sync(0xffffffffu, keep);
+                const int nk = __popc(kept);
+                if (sp + nk <= kStackDepth) {
+                    if (keep) stk[sp + nk - 1 - __popc(kept & below)] = fc + static_cast<int32_t>(lane);
+                    sp += nk;
                 } else {
                     guard_ok = false;
                 }
+                __syncwarp();
             }
         } else {
-            // a leaf: every lane tests every point against its own centre
-            const bool need = cls != 0;
+            // a leaf: every lane tests every point against its own centre; a lane whose
+            // kernel misses the leaf's box gets no hits (the same monotonicity), so only
+            // the lanes that already took an enclosing range are masked out
+            const bool need = active && end > taken_below;
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
                 uint32_t hits = 0;
@@ -146,7 +179,12 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
                     hits |= static_cast<uint32_t>(in) << t;
                 }
                 if (!need) hits = 0;
+                count += __popc(hits);
                 if (FILL) {
+                    if (out + __popc(hits) > out_end) {  // never true when the count pass agrees
+                        guard_ok = false;
+                        hits = 0;
+                    }
                     const int32_t my_id = lane < m ? static_cast<int32_t>(a.perm[base + lane]) : 0;
                     unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
                     while (todo) {
@@ -154,16 +192,10 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
                         todo &= todo - 1;
                         const uint32_t h = __shfl_sync(0xffffffffu, hits, src);
                         const int64_t o = __shfl_sync(0xffffffffu, out, src);
-                        const int64_t e = __shfl_sync(0xffffffffu, out_end, src);
-                        if ((h >> lane) & 1u) {
-                            const int64_t pos = o + __popc(h & below);
-                            if (pos < e) a.cols[pos] = my_id;
-                            else guard_ok = false;
-                        }
+                        if ((h >> lane) & 1u) a.cols[o + __popc(h & below)] = my_id;
                     }
                     out += __popc(hits);
                 }
-                count += __popc(hits);
             }
         }
     }
