@@ -62,12 +62,14 @@ template <int KMAX>
 struct BestList {
     uint64_t key[KMAX];
     uint64_t kth;  // the k-th pair
-    __device__ __forceinline__ void init() {
+    int k;
+    __device__ __forceinline__ void init(int kk) {
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) key[s] = kNoPair;
         kth = kNoPair;
+        k = kk;
     }
-    __device__ __forceinline__ void insert(uint64_t nk, int k) {
+    __device__ __forceinline__ void insert(uint64_t nk) {
         bool stays[KMAX];
 #pragma unroll
         for (int s = 0; s < KMAX; ++s) stays[s] = key[s] < nk;
@@ -96,12 +98,72 @@ struct BestList {
     }
 };
 
+// The k best pairs of one lane as a max-heap in shared memory (root = the k-th pair,
+// the pruning bound), lane-interleaved: slot s of lane l is word s * 32 + l, so the 32
+// lanes of a warp always touch 32 different banks whatever slots they visit.  Replacing
+// the root and sifting it down costs O(log k); finish() heap-sorts the slots ascending.
+struct LaneHeap {
+    uint64_t* slot0;  // &heap[0][lane]
+    uint64_t kth;     // register copy of the root
+    int k;
+    __device__ __forceinline__ uint64_t& at(int s) const { return slot0[s * 32]; }
+    __device__ __forceinline__ void init(uint64_t* base, int kk) {
+        slot0 = base;
+        k = kk;
+        for (int s = 0; s < k; ++s) at(s) = kNoPair;
+        kth = kNoPair;
+    }
+    // place x at the root of the heap of the first `size` slots and restore the order
+    __device__ __forceinline__ void sift_down(uint64_t x, int size) {
+        int pos = 0;
+        for (;;) {
+            const int l = 2 * pos + 1;
+            if (l >= size) break;
+            int c = l;
+            uint64_t cv = at(l);
+            if (l + 1 < size) {
+                const uint64_t rv = at(l + 1);
+                if (rv > cv) {
+                    c = l + 1;
+                    cv = rv;
+                }
+            }
+            if (cv <= x) break;
+            at(pos) = cv;
+            pos = c;
+        }
+        at(pos) = x;
+    }
+    __device__ __forceinline__ void insert(uint64_t nk) {  // requires nk < kth
+        sift_down(nk, k);
+        kth = at(0);
+    }
+    __device__ __forceinline__ void finish() {
+        for (int end = k - 1; end > 0; --end) {
+            const uint64_t top = at(0);
+            const uint64_t last = at(end);
+            at(end) = top;
+            sift_down(last, end);
+        }
+    }
+    __device__ __forceinline__ float kth_d2() const { return __uint_as_float(static_cast<uint32_t>(kth >> 32)); }
+    __device__ __forceinline__ void store(const KnnArgs& a, uint32_t row) const {
+        const int64_t base = static_cast<int64_t>(row) * a.k;
+        for (int s = 0; s < k; ++s) {
+            const uint64_t key = at(s);
+            const uint32_t id = static_cast<uint32_t>(key);
+            a.out_idx[base + s] = id == kNoIndex ? -1 : static_cast<int32_t>(id);
+            a.out_d2[base + s] = __uint_as_float(static_cast<uint32_t>(key >> 32));
+        }
+    }
+};
+
 // Test the points at sorted positions [lo, hi) against every lane's centre and insert the
 // better ones: pass 1 marks, per 32-point chunk, the points that beat the lane's current
 // k-th pair; pass 2 lets each lane insert its marked points.
-template <int KMAX>
+template <class List>
 __device__ __forceinline__ void scan_points(const KnnArgs& a, uint32_t lo, uint32_t hi, const float4& c, bool need,
-                                            BestList<KMAX>& best) {
+                                            List& best) {
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t m = min(32u, hi - base);
         uint32_t cand = 0;
@@ -119,7 +181,7 @@ __device__ __forceinline__ void scan_points(const KnnArgs& a, uint32_t lo, uint3
                 const float4 p = __ldg(&a.pts[base + t]);
                 const uint64_t nk =
                     pair_key(sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z)), __float_as_uint(p.w));
-                if (nk < best.kth) best.insert(nk, a.k);
+                if (nk < best.kth) best.insert(nk);
             }
         }
     }
@@ -142,18 +204,19 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
 }
 
 // resident blocks per SM the register budget is sized for (4 warps each)
+// warps per block of the group kernel: the heaps take KMAX * 256 bytes per warp
 template <int KMAX>
-struct KnnOccupancy {
-    static constexpr int kBlocks = KMAX <= 8 ? 8 : (KMAX <= 16 ? 5 : (KMAX <= 32 ? 3 : 2));
-};
+__host__ __device__ constexpr int knn_warps() { return KMAX >= 64 ? 2 : kKnnWarps; }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kKnnWarps * 32, KnnOccupancy<KMAX>::kBlocks) k_knn_group(KnnArgs a) {
-    __shared__ int32_t stack[kKnnWarps][kStackDepth];
+__global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a) {
+    constexpr int kWarps = knn_warps<KMAX>();
+    __shared__ int32_t stack[kWarps][kStackDepth];
+    __shared__ uint64_t heaps[kWarps][KMAX][32];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     int32_t* stk = stack[warp];
-    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kKnnWarps + warp) * 32;
+    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kWarps + warp) * 32;
     if (first >= a.nq) return;
     const int64_t qi = first + lane;
     const bool active = qi < a.nq;
@@ -180,8 +243,8 @@ __global__ void __launch_bounds__(kKnnWarps * 32, KnnOccupancy<KMAX>::kBlocks) k
     }
     gx *= inv; gy *= inv; gz *= inv;
 
-    BestList<KMAX> best;
-    best.init();
+    LaneHeap best;
+    best.init(&heaps[warp][0][lane], a.k);
 
     // All-points search on a cloud ordered along the curve: the centres are the points
     // at positions first .. first + 31, and their curve neighbours are mostly their space
@@ -192,7 +255,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, KnnOccupancy<KMAX>::kBlocks) k
         win_lo = static_cast<uint32_t>(first > a.window ? first - a.window : 0);
         const int64_t hi = first + 32 + a.window;
         win_hi = static_cast<uint32_t>(hi < a.nq ? hi : a.nq);
-        scan_points<KMAX>(a, win_lo, win_hi, c, active, best);
+        scan_points(a, win_lo, win_hi, c, active, best);
     }
 
     bool guard_ok = true;
@@ -246,11 +309,14 @@ __global__ void __launch_bounds__(kKnnWarps * 32, KnnOccupancy<KMAX>::kBlocks) k
             __syncwarp();
         } else {
             // the leaf's points outside the seeding window
-            scan_points<KMAX>(a, start, min(end, win_lo > start ? win_lo : start), c, need, best);
-            scan_points<KMAX>(a, max(start, win_hi), end, c, need, best);
+            scan_points(a, start, min(end, win_lo > start ? win_lo : start), c, need, best);
+            scan_points(a, max(start, win_hi), end, c, need, best);
         }
     }
-    if (active) best.store(a, row);
+    if (active) {
+        best.finish();
+        best.store(a, row);
+    }
     if (!guard_ok && lane == 0) atomicOr(a.err, kGuardTripped);
 }
 
@@ -261,7 +327,7 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
     const float4 c = a.q[qi];
     const uint32_t row = __float_as_uint(c.w);
     BestList<KMAX> best;
-    best.init();
+    best.init(a.k);
     int32_t stk[kStackDepth];
     int sp = 1;
     stk[0] = 0;
@@ -300,7 +366,7 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
                 const uint32_t id = a.perm[j];
                 const float4 p = a.pts[id];
                 const uint64_t nk = pair_key(sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z)), id);
-                if (nk < best.kth) best.insert(nk, a.k);
+                if (nk < best.kth) best.insert(nk);
             }
         }
     }
@@ -313,7 +379,8 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
     if (t->enc == SFC_ENC_NONE) {
         SFC_LAUNCH("knn", s, k_knn_lane<KMAX>, grid_for(a.nq, 128), 128, 0, a);
     } else {
-        SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for((a.nq + 31) / 32, kKnnWarps), kKnnWarps * 32, 0, a);
+        constexpr int kWarps = knn_warps<KMAX>();
+        SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for((a.nq + 31) / 32, kWarps), kWarps * 32, 0, a);
     }
     return SFC_OK;
 }
