@@ -467,6 +467,7 @@ static void free_octree(Octree* t, cudaStream_t s) {
     dev_free(t->leaves, s);
     dev_free(t->leaf_counts, s);
     dev_free(t->scal, s);
+    release_records(t, s);
 }
 
 static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {

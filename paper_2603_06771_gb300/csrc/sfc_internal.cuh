@@ -46,6 +46,21 @@ struct BuildScalars {
     float ext;
 };
 
+// Hit masks recorded by an all-points count pass for the fill pass that follows with the
+// same radius and kernel (see sfc_radius.cu).  Owned by the handle, released by the
+// fill pass that consumes it or by octree_free.
+struct RadiusRecords {
+    uint32_t* masks = nullptr;   // [groups][cap][32] per-lane hit masks
+    uint2* head = nullptr;       // [groups][cap] record headers
+    uint32_t* count = nullptr;   // [groups] records of the group, kRecordsOverflow if they did not fit
+    int64_t groups = 0;
+    int cap = 0;
+    float r = 0.f;
+    int kern = -1;
+    bool valid = false;
+};
+constexpr uint32_t kRecordsOverflow = 0xffffffffu;
+
 struct Octree {
     int device = 0;
     int64_t n = 0;
@@ -65,7 +80,10 @@ struct Octree {
     int64_t n_internal = 0, n_nodes = 0, n_leaves = 0;
     float lo[3] = {0, 0, 0};
     float scale = 1;
+    RadiusRecords records;
 };
+
+void release_records(Octree* t, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // runtime (sfc_runtime.cu)

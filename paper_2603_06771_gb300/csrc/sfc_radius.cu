@@ -11,6 +11,13 @@
 // unordered cloud (SFC_ENC_NONE) the 32 centres of a warp are scattered, so each lane
 // walks the tree on its own and reads points through the permutation.
 //
+// Count and fill.  The fill pass must repeat the count pass's decisions exactly.  For
+// all-points searches the count pass records, per warp, every leaf chunk that produced a
+// hit (its position and the 32 lanes' hit masks) and every node taken whole, in walk
+// order; the fill pass replays those records and only writes.  A warp whose records do
+// not fit its slots walks the tree again in the fill pass (the same code, the same
+// decisions).
+//
 // Exactness of the box tests.  Each node stores the tight bounding box of its points.
 // Rounding to nearest is monotone, so with d = fl(p - c) per axis: the box point
 // nearest to c (the clamp of section 3.3) has the smallest |d| on every axis, and one of
@@ -20,6 +27,7 @@
 // step 1a).  Both shortcuts therefore give exactly the per-point result.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include "sfc_internal.cuh"
 
@@ -41,7 +49,17 @@ struct RadiusArgs {
     int32_t* cols;
     unsigned int* err;                  // kGuardTripped is or-ed in when a guard fails
     int64_t max_steps;                  // nodes of the tree: a walk pops each node once at most
+    // hit-mask records: mode 1 = this count pass records them, 2 = this fill pass replays
+    int rec_mode;
+    int rec_cap;
+    uint32_t* rec_masks;
+    uint2* rec_head;
+    uint32_t* rec_count;
 };
+
+// A record header is (chunk start, chunk size <= 32) for a leaf chunk, or
+// (range start, kRangeBit | range end) for a node taken whole (step 1a).
+constexpr uint32_t kRangeBit = 0x80000000u;
 
 // 0: no point of the box is inside the kernel; 2: every point is (asked only with
 // prune); 1: undecided.
@@ -73,7 +91,8 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     int32_t* stk = stack[warp];
-    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp) * 32;
+    const int64_t group = static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp;
+    const int64_t first = group * 32;
     if (first >= a.nq) return;  // whole warp
     const int64_t qi = first + lane;
     const bool active = qi < a.nq;
@@ -84,8 +103,86 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
     uint32_t count = 0;
     int64_t out = (FILL && active) ? a.row_ptr[row] : 0;
     const int64_t out_end = (FILL && active) ? a.row_ptr[row + 1] : 0;
-    uint32_t taken_below = 0;  // positions below this were emitted as a whole range
     bool guard_ok = true;
+
+    // ---- emitting (shared by the walk and the replay)
+    // the lanes of `whole` take [start, end) (step 1a)
+    auto take_range = [&](unsigned int whole, uint32_t start, uint32_t end, bool mine) {
+        if (FILL) {
+            unsigned int todo = whole;
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t o = __shfl_sync(0xffffffffu, out, src);
+                const int64_t e = __shfl_sync(0xffffffffu, out_end, src);
+                if (o + (end - start) > e) {
+                    guard_ok = false;
+                    continue;
+                }
+                for (uint32_t j = start + lane; j < end; j += 32)
+                    a.cols[o + (j - start)] = static_cast<int32_t>(a.perm[j]);
+            }
+        }
+        if (mine) {
+            count += end - start;
+            out += end - start;
+        }
+    };
+    // the hits of a leaf chunk [base, base + m): lane i's row gets the points of its mask
+    auto take_hits = [&](uint32_t hits, uint32_t base, uint32_t m) {
+        count += __popc(hits);
+        if (FILL) {
+            if (out + __popc(hits) > out_end) {  // never true when the count pass agrees
+                guard_ok = false;
+                hits = 0;
+            }
+            const int32_t my_id = lane < m ? static_cast<int32_t>(a.perm[base + lane]) : 0;
+            unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t h = __shfl_sync(0xffffffffu, hits, src);
+                const int64_t o = __shfl_sync(0xffffffffu, out, src);
+                if ((h >> lane) & 1u) a.cols[o + __popc(h & below)] = my_id;
+            }
+            out += __popc(hits);
+        }
+    };
+
+    // ---- replay of the count pass's records
+    if (FILL && a.rec_mode == 2) {
+        const uint32_t nrec = a.rec_count[group];
+        if (nrec <= static_cast<uint32_t>(a.rec_cap)) {  // else the records overflowed: walk again
+            for (uint32_t k = 0; k < nrec; ++k) {
+                const int64_t slot = group * a.rec_cap + k;
+                const uint2 hd = a.rec_head[slot];
+                const uint32_t mask = active ? a.rec_masks[slot * 32 + lane] : 0u;
+                if (hd.y & kRangeBit) {
+                    take_range(__ballot_sync(0xffffffffu, mask != 0), hd.x, hd.y & ~kRangeBit, mask != 0);
+                } else {
+                    take_hits(mask, hd.x, hd.y);
+                }
+            }
+            if (!guard_ok) atomicOr(a.err, kGuardTripped);
+            return;
+        }
+    }
+
+    // ---- the walk
+    uint32_t nrec = 0;
+    bool rec_overflow = false;
+    auto record = [&](uint32_t hx, uint32_t hy, uint32_t mask) {
+        if (nrec < static_cast<uint32_t>(a.rec_cap)) {
+            const int64_t slot = group * a.rec_cap + nrec;
+            a.rec_masks[slot * 32 + lane] = mask;
+            if (lane == 0) a.rec_head[slot] = make_uint2(hx, hy);
+        } else {
+            rec_overflow = true;
+        }
+        ++nrec;
+    };
+    const bool recording = !FILL && a.rec_mode == 1;
+    uint32_t taken_below = 0;  // positions below this were emitted as a whole range
 
     // bounding box of the group's centres
     float glx = active ? c.x : INFINITY, gly = active ? c.y : INFINITY, glz = active ? c.z : INFINITY;
@@ -120,27 +217,9 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
             const unsigned int partial = __ballot_sync(0xffffffffu, cls == 1);
             const unsigned int whole = __ballot_sync(0xffffffffu, cls == 2);
             if (whole) {
-                // step 1a: the node lies inside these lanes' kernels; emit its range
-                if (FILL) {
-                    unsigned int todo = whole;
-                    while (todo) {
-                        const int src = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int64_t o = __shfl_sync(0xffffffffu, out, src);
-                        const int64_t e = __shfl_sync(0xffffffffu, out_end, src);
-                        if (o + (end - start) > e) {
-                            guard_ok = false;
-                            continue;
-                        }
-                        for (uint32_t j = start + lane; j < end; j += 32)
-                            a.cols[o + (j - start)] = static_cast<int32_t>(a.perm[j]);
-                    }
-                }
-                if (cls == 2) {
-                    count += end - start;
-                    out += end - start;
-                    taken_below = end;
-                }
+                take_range(whole, start, end, cls == 2);
+                if (recording) record(start, kRangeBit | end, cls == 2 ? 0xffffffffu : 0u);
+                if (cls == 2) taken_below = end;
             }
             if (partial) {
                 // keep the non-empty children that some centre of the group may reach;
@@ -179,27 +258,13 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
                     hits |= static_cast<uint32_t>(in) << t;
                 }
                 if (!need) hits = 0;
-                count += __popc(hits);
-                if (FILL) {
-                    if (out + __popc(hits) > out_end) {  // never true when the count pass agrees
-                        guard_ok = false;
-                        hits = 0;
-                    }
-                    const int32_t my_id = lane < m ? static_cast<int32_t>(a.perm[base + lane]) : 0;
-                    unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
-                    while (todo) {
-                        const int src = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const uint32_t h = __shfl_sync(0xffffffffu, hits, src);
-                        const int64_t o = __shfl_sync(0xffffffffu, out, src);
-                        if ((h >> lane) & 1u) a.cols[o + __popc(h & below)] = my_id;
-                    }
-                    out += __popc(hits);
-                }
+                if (recording && __ballot_sync(0xffffffffu, hits != 0)) record(base, m, hits);
+                take_hits(hits, base, m);
             }
         }
     }
     if (!FILL && active) a.counts[row] = count;
+    if (recording && lane == 0) a.rec_count[group] = rec_overflow ? kRecordsOverflow : nrec;
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
 }
 
@@ -306,6 +371,11 @@ static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, flo
     a.cols = nullptr;
     a.err = &t->scal->bad;
     a.max_steps = t->n_nodes;
+    a.rec_mode = 0;
+    a.rec_cap = 0;
+    a.rec_masks = nullptr;
+    a.rec_head = nullptr;
+    a.rec_count = nullptr;
     return a;
 }
 
@@ -327,8 +397,39 @@ static sfc_status check_radius_args(sfc_octree h, const float* queries, int64_t 
     return SFC_OK;
 }
 
-static sfc_status count_impl(const Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
-                             Scratch& scratch, int64_t* row_ptr, const unsigned int* bad, int64_t* nnz) {
+// record slots per warp of 32 centres (a warp that needs more walks again in the fill)
+constexpr int kRecordCap = 32;
+
+// Allocate the hit-mask records of an all-points count pass (ordered encodings only);
+// without memory for them the fill pass simply walks the tree again.
+static void setup_records(Octree* t, int64_t rows, float r, int kern, cudaStream_t s, RadiusArgs& a) {
+    release_records(t, s);
+    if (t->enc == SFC_ENC_NONE) return;
+    RadiusRecords& rec = t->records;
+    const int64_t groups = (rows + 31) / 32;
+    const int64_t slots = groups * kRecordCap;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&rec.masks), sizeof(uint32_t) * 32 * slots, s) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&rec.head), sizeof(uint2) * slots, s) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&rec.count), sizeof(uint32_t) * groups, s) != cudaSuccess) {
+        cudaGetLastError();
+        release_records(t, s);
+        return;
+    }
+    rec.groups = groups;
+    rec.cap = kRecordCap;
+    rec.r = r;
+    rec.kern = kern;
+    rec.valid = false;  // set once the recording pass is launched
+    a.rec_mode = 1;
+    a.rec_cap = kRecordCap;
+    a.rec_masks = rec.masks;
+    a.rec_head = rec.head;
+    a.rec_count = rec.count;
+}
+
+static sfc_status count_impl(Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
+                             Scratch& scratch, int64_t* row_ptr, const unsigned int* bad, int64_t* nnz,
+                             bool all_points) {
     if (!(r > 0.f) || rows == 0 || t->n == 0) {
         SFC_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (rows + 1), s));
     } else {
@@ -336,7 +437,13 @@ static sfc_status count_impl(const Octree* t, const float4* q4, int64_t rows, fl
         SFC_TRY(scratch.alloc(&counts, rows));
         RadiusArgs a = make_args(t, q4, rows, r);
         a.counts = counts;
-        SFC_TRY(launch_search<false>(t, a, kern, s));
+        if (all_points) setup_records(t, rows, r, kern, s, a);
+        const sfc_status st = launch_search<false>(t, a, kern, s);
+        if (st != SFC_OK) {
+            release_records(t, s);
+            return st;
+        }
+        if (a.rec_mode == 1) t->records.valid = true;
         SFC_TRY(scan_u32_to_i64(counts, row_ptr, rows, s, scratch));
     }
     unsigned int hbad = 0, herr = 0;
@@ -367,13 +474,27 @@ sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_
     return (herr & kGuardTripped) ? SFC_ERR_INTERNAL : SFC_OK;
 }
 
-static sfc_status fill_impl(const Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
-                            const int64_t* row_ptr, int32_t* cols) {
+static sfc_status fill_impl(Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
+                            const int64_t* row_ptr, int32_t* cols, bool all_points) {
     if (!(r > 0.f) || rows == 0 || t->n == 0) return SFC_OK;
     RadiusArgs a = make_args(t, q4, rows, r);
     a.row_ptr = row_ptr;
     a.cols = cols;
-    return launch_search<true>(t, a, kern, s);
+    const RadiusRecords& rec = t->records;
+    uint32_t rb, qb;
+    memcpy(&rb, &rec.r, sizeof rb);
+    memcpy(&qb, &r, sizeof qb);
+    const bool replay = all_points && rec.valid && rec.kern == kern && rb == qb && rec.groups == (rows + 31) / 32;
+    if (replay) {
+        a.rec_mode = 2;
+        a.rec_cap = rec.cap;
+        a.rec_masks = rec.masks;
+        a.rec_head = rec.head;
+        a.rec_count = rec.count;
+    }
+    const sfc_status st = launch_search<true>(t, a, kern, s);
+    if (replay) release_records(t, s);  // stream-ordered after the replay
+    return st;
 }
 
 static sfc_status check_guard(const Octree* t, cudaStream_t s) {
@@ -393,6 +514,13 @@ static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, c
     return prepare_queries(t, queries, rows, s, scratch, q4, *bad);
 }
 
+void release_records(Octree* t, cudaStream_t s) {
+    dev_free(t->records.masks, s);
+    dev_free(t->records.head, s);
+    dev_free(t->records.count, s);
+    t->records = RadiusRecords();
+}
+
 }  // namespace sfc
 
 using sfc::Octree;
@@ -410,7 +538,7 @@ sfc_status radius_count(sfc_octree h, const float* queries_xyz, int64_t n_querie
     const float4* q4 = nullptr;
     unsigned int* bad = nullptr;
     SFC_TRY(sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad));
-    return sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, nnz);
+    return sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, nnz, queries_xyz == nullptr);
 }
 
 sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
@@ -424,7 +552,7 @@ sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries
     const float4* q4 = nullptr;
     unsigned int* bad = nullptr;
     SFC_TRY(sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad));
-    return sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols);
+    return sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols, queries_xyz == nullptr);
 }
 
 sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
@@ -447,9 +575,10 @@ sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queri
         unsigned int* bad = nullptr;
         st = sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad);
         if (st == SFC_OK) st = sfc::dev_alloc(&row_ptr, rows + 1, s);
-        if (st == SFC_OK) st = sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, &nnz);
+        const bool all = queries_xyz == nullptr;
+        if (st == SFC_OK) st = sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, row_ptr, bad, &nnz, all);
         if (st == SFC_OK) st = sfc::dev_alloc(&cols, nnz, s);
-        if (st == SFC_OK) st = sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols);
+        if (st == SFC_OK) st = sfc::fill_impl(&h->tree, q4, rows, r, kern, s, row_ptr, cols, all);
         if (st == SFC_OK) st = sfc::check_guard(&h->tree, s);
     }
     if (st != SFC_OK) {
