@@ -113,9 +113,8 @@ struct LaneHeap {
         for (int s = 0; s < k; ++s) at(s) = kNoPair;
         kth = kNoPair;
     }
-    // place x at the root of the heap of the first `size` slots and restore the order
-    __device__ __forceinline__ void sift_down(uint64_t x, int size) {
-        int pos = 0;
+    // place x at slot pos of the heap of the first `size` slots and restore the order below it
+    __device__ __forceinline__ void sift_down(uint64_t x, int size, int pos = 0) {
         for (;;) {
             const int l = 2 * pos + 1;
             if (l >= size) break;
@@ -136,6 +135,11 @@ struct LaneHeap {
     }
     __device__ __forceinline__ void insert(uint64_t nk) {  // requires nk < kth
         sift_down(nk, k);
+        kth = at(0);
+    }
+    // the k slots hold arbitrary pairs: restore the heap order bottom-up
+    __device__ __forceinline__ void heapify() {
+        for (int i = k / 2 - 1; i >= 0; --i) sift_down(at(i), k, i);
         kth = at(0);
     }
     __device__ __forceinline__ void finish() {
@@ -161,9 +165,10 @@ struct LaneHeap {
 // Test the points at sorted positions [lo, hi) against every lane's centre and insert the
 // better ones: pass 1 marks, per 32-point chunk, the points that beat the lane's current
 // k-th pair; pass 2 lets each lane insert its marked points.
+// Points at positions in [skip_lo, skip_lo + skip_n) were already offered to this lane.
 template <class List>
 __device__ __forceinline__ void scan_points(const KnnArgs& a, uint32_t lo, uint32_t hi, const float4& c, bool need,
-                                            List& best) {
+                                            List& best, int64_t skip_lo = 0, uint32_t skip_n = 0) {
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t m = min(32u, hi - base);
         uint32_t cand = 0;
@@ -171,7 +176,8 @@ __device__ __forceinline__ void scan_points(const KnnArgs& a, uint32_t lo, uint3
         for (uint32_t t = 0; t < m; ++t) {
             const float4 p = __ldg(&a.pts[base + t]);
             const float d = sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z));
-            if (pair_key(d, __float_as_uint(p.w)) < best.kth) cand |= 1u << t;
+            const bool seen = static_cast<uint64_t>(static_cast<int64_t>(base + t) - skip_lo) < skip_n;
+            if (pair_key(d, __float_as_uint(p.w)) < best.kth && !seen) cand |= 1u << t;
         }
         if (!need) cand = 0;
         while (__ballot_sync(0xffffffffu, cand != 0)) {
@@ -204,6 +210,11 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
 }
 
 // resident blocks per SM the register budget is sized for (4 warps each)
+// Candidate chunks a lane found during the walk wait in a per-lane queue (chunk base,
+// candidate mask) and are inserted in batches: insertion rounds then follow the lanes'
+// total candidates instead of the largest count in every single chunk.
+constexpr int kQueueCap = 8;
+
 // warps per block of the group kernel: the heaps take KMAX * 256 bytes per warp
 template <int KMAX>
 __host__ __device__ constexpr int knn_warps() { return KMAX >= 64 ? 2 : kKnnWarps; }
@@ -213,6 +224,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     constexpr int kWarps = knn_warps<KMAX>();
     __shared__ int32_t stack[kWarps][kStackDepth];
     __shared__ uint64_t heaps[kWarps][KMAX][32];
+    __shared__ uint2 queue[kWarps][kQueueCap][32];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     int32_t* stk = stack[warp];
@@ -246,17 +258,81 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     LaneHeap best;
     best.init(&heaps[warp][0][lane], a.k);
 
-    // All-points search on a cloud ordered along the curve: the centres are the points
-    // at positions first .. first + 31, and their curve neighbours are mostly their space
-    // neighbours.  Seeding every list with the points of a window around those positions
-    // gives a near-final k-th distance before the walk; the walk skips the window.
-    uint32_t win_lo = 0, win_hi = 0;
+    // All-points search on a cloud ordered along the curve: lane l's centre is the point at
+    // position p = first + l, and its curve neighbours are mostly its space neighbours.
+    // Each lane first offers its list the points at p, p+1, p-1, p+2, ... (a window of
+    // 2 * window positions, nearest along the curve first, so that few later points beat
+    // the list), which gives a near-final k-th distance before the walk; the walk then
+    // skips those positions.  In step t all lanes read consecutive positions.
+    int64_t win_lo = 0;
+    uint32_t win_n = 0;
     if (a.window > 0) {
-        win_lo = static_cast<uint32_t>(first > a.window ? first - a.window : 0);
-        const int64_t hi = first + 32 + a.window;
-        win_hi = static_cast<uint32_t>(hi < a.nq ? hi : a.nq);
-        scan_points(a, win_lo, win_hi, c, active, best);
+        const int64_t p = qi;
+        win_lo = p - a.window + 1;
+        win_n = static_cast<uint32_t>(2 * a.window);
+        // the k nearest positions along the curve fill the heap directly
+        auto window_pos = [&](int t) { return p + ((t & 1) ? (t + 1) / 2 : -(t / 2)); };
+        const int k = a.k;
+        for (int t = 0; t < k; ++t) {
+            const int64_t pos = window_pos(t);
+            uint64_t key = kNoPair;
+            if (active && pos >= 0 && pos < a.nq) {
+                const float4 q = __ldg(&a.pts[pos]);
+                key = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
+                               __float_as_uint(q.w));
+            }
+            best.at(t) = key;
+        }
+        best.heapify();
+        for (int t0 = k; t0 < 2 * a.window; t0 += 32) {
+            uint32_t cand = 0;
+            const int span = min(32, 2 * static_cast<int>(a.window) - t0);
+#pragma unroll 4
+            for (int u = 0; u < span; ++u) {
+                const int64_t pos = window_pos(t0 + u);
+                if (active && pos >= 0 && pos < a.nq) {
+                    const float4 q = __ldg(&a.pts[pos]);
+                    const float d = sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
+                    if (pair_key(d, __float_as_uint(q.w)) < best.kth) cand |= 1u << u;
+                }
+            }
+            while (__ballot_sync(0xffffffffu, cand != 0)) {
+                if (cand) {
+                    const int u = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    const int64_t pos = window_pos(t0 + u);
+                    const float4 q = __ldg(&a.pts[pos]);
+                    const uint64_t nk = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
+                                                 __float_as_uint(q.w));
+                    if (nk < best.kth) best.insert(nk);
+                }
+            }
+        }
     }
+
+    int queued = 0;  // entries in this lane's queue
+    auto drain = [&]() {
+        __syncwarp();
+        int e = 0;
+        uint32_t base = 0, cand = 0;
+        while (__ballot_sync(0xffffffffu, cand != 0 || e < queued)) {
+            if (cand == 0 && e < queued) {
+                const uint2 entry = queue[warp][e++][lane];
+                base = entry.x;
+                cand = entry.y;
+            }
+            if (cand) {
+                const int t = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const float4 q = __ldg(&a.pts[base + t]);
+                const uint64_t nk = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
+                                             __float_as_uint(q.w));
+                if (nk < best.kth) best.insert(nk);
+            }
+        }
+        queued = 0;
+        __syncwarp();
+    };
 
     bool guard_ok = true;
     int sp = 1;
@@ -308,11 +384,23 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
             }
             __syncwarp();
         } else {
-            // the leaf's points outside the seeding window
-            scan_points(a, start, min(end, win_lo > start ? win_lo : start), c, need, best);
-            scan_points(a, max(start, win_hi), end, c, need, best);
+            for (uint32_t base = start; base < end; base += 32) {
+                const uint32_t m = min(32u, end - base);
+                uint32_t cand = 0;
+#pragma unroll 4
+                for (uint32_t t = 0; t < m; ++t) {
+                    const float4 q = __ldg(&a.pts[base + t]);
+                    const float d = sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
+                    const bool seen = static_cast<uint64_t>(static_cast<int64_t>(base + t) - win_lo) < win_n;
+                    if (pair_key(d, __float_as_uint(q.w)) < best.kth && !seen) cand |= 1u << t;
+                }
+                if (!need) cand = 0;
+                if (cand) queue[warp][queued++][lane] = make_uint2(base, cand);
+                if (__ballot_sync(0xffffffffu, queued == kQueueCap)) drain();
+            }
         }
     }
+    drain();
     if (active) {
         best.finish();
         best.store(a, row);
