@@ -210,30 +210,41 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
 }
 
 // resident blocks per SM the register budget is sized for (4 warps each)
-// Candidate chunks a lane found during the walk wait in a per-lane queue (chunk base,
-// candidate mask) and are inserted in batches: insertion rounds then follow the lanes'
-// total candidates instead of the largest count in every single chunk.
-constexpr int kQueueCap = 8;
-
 // warps per block of the group kernel: the heaps take KMAX * 256 bytes per warp
 template <int KMAX>
 __host__ __device__ constexpr int knn_warps() { return KMAX >= 64 ? 2 : kKnnWarps; }
 
+__device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
+    NodeBox o;
+    o.lo = make_float4(__shfl_sync(0xffffffffu, b.lo.x, src), __shfl_sync(0xffffffffu, b.lo.y, src),
+                       __shfl_sync(0xffffffffu, b.lo.z, src), __shfl_sync(0xffffffffu, b.lo.w, src));
+    o.hi = make_float4(__shfl_sync(0xffffffffu, b.hi.x, src), __shfl_sync(0xffffffffu, b.hi.y, src),
+                       __shfl_sync(0xffffffffu, b.hi.z, src), __shfl_sync(0xffffffffu, b.hi.w, src));
+    return o;
+}
+
+// Group kNN walk.  Stack entries carry (first child, point range, lanes needing the node),
+// decided when the parent was expanded, so a pop reads shared memory only; an expansion
+// loads the eight children once (lanes 0-7).  Points (the seeding window, leaf chunks) are
+// staged in shared memory with coalesced loads, and both the tests and the insertions read
+// them there.  Per chunk, pass 1 marks the points that beat each lane's current k-th pair
+// and pass 2 lets each lane insert its marked points.
 template <int KMAX>
 __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a) {
     constexpr int kWarps = knn_warps<KMAX>();
-    __shared__ int32_t stack[kWarps][kStackDepth];
+    constexpr int kBuf = 96;  // staged points: the seeding window (3 x 32) or one leaf chunk
+    __shared__ int4 stack_e[kWarps][kStackDepth];  // first child, start, end, lanes needing it
     __shared__ uint64_t heaps[kWarps][KMAX][32];
-    __shared__ uint2 queue[kWarps][kQueueCap][32];
+    __shared__ float4 pbuf[kWarps][kBuf];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    int32_t* stk = stack[warp];
     const int64_t first = (static_cast<int64_t>(blockIdx.x) * kWarps + warp) * 32;
     if (first >= a.nq) return;
     const int64_t qi = first + lane;
     const bool active = qi < a.nq;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t row = __float_as_uint(c.w);
+    float4* buf = pbuf[warp];
 
     // centre (orders the walk) and bounding box (prunes it) of the group's centres
     const unsigned int act = __ballot_sync(0xffffffffu, active);
@@ -257,109 +268,90 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
 
     LaneHeap best;
     best.init(&heaps[warp][0][lane], a.k);
+    auto key_of = [&](const float4& q) {
+        return pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)), __float_as_uint(q.w));
+    };
 
     // All-points search on a cloud ordered along the curve: lane l's centre is the point at
-    // position p = first + l, and its curve neighbours are mostly its space neighbours.
-    // Each lane first offers its list the points at p, p+1, p-1, p+2, ... (a window of
-    // 2 * window positions, nearest along the curve first, so that few later points beat
-    // the list), which gives a near-final k-th distance before the walk; the walk then
-    // skips those positions.  In step t all lanes read consecutive positions.
+    // position p = first + l, and its curve neighbours are mostly its space neighbours.  Each
+    // lane first offers its list the points at p, p+1, p-1, p+2, ... (2 * window positions,
+    // nearest along the curve first): the k nearest fill the heap directly, the others are
+    // offered in turn.  That gives a near-final k-th distance before the walk, which then
+    // skips those positions.
     int64_t win_lo = 0;
     uint32_t win_n = 0;
     if (a.window > 0) {
+        const int64_t r0 = first - (a.window - 1);  // staged positions r0 .. r0 + 95
+        for (int j = lane; j < kBuf; j += 32) {
+            const int64_t pos = r0 + j;
+            buf[j] = (pos >= 0 && pos < a.nq) ? __ldg(&a.pts[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
         const int64_t p = qi;
         win_lo = p - a.window + 1;
         win_n = static_cast<uint32_t>(2 * a.window);
-        // the k nearest positions along the curve fill the heap directly
-        auto window_pos = [&](int t) { return p + ((t & 1) ? (t + 1) / 2 : -(t / 2)); };
+        auto window_key = [&](int t) -> uint64_t {
+            const int64_t pos = p + ((t & 1) ? (t + 1) / 2 : -(t / 2));
+            if (!active || pos < 0 || pos >= a.nq) return kNoPair;
+            return key_of(buf[pos - r0]);
+        };
         const int k = a.k;
-        for (int t = 0; t < k; ++t) {
-            const int64_t pos = window_pos(t);
-            uint64_t key = kNoPair;
-            if (active && pos >= 0 && pos < a.nq) {
-                const float4 q = __ldg(&a.pts[pos]);
-                key = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
-                               __float_as_uint(q.w));
-            }
-            best.at(t) = key;
-        }
+        for (int t = 0; t < k; ++t) best.at(t) = window_key(t);
         best.heapify();
         for (int t0 = k; t0 < 2 * a.window; t0 += 32) {
-            uint32_t cand = 0;
             const int span = min(32, 2 * static_cast<int>(a.window) - t0);
-#pragma unroll 4
-            for (int u = 0; u < span; ++u) {
-                const int64_t pos = window_pos(t0 + u);
-                if (active && pos >= 0 && pos < a.nq) {
-                    const float4 q = __ldg(&a.pts[pos]);
-                    const float d = sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
-                    if (pair_key(d, __float_as_uint(q.w)) < best.kth) cand |= 1u << u;
-                }
-            }
+            uint32_t cand = 0;
+#pragma unroll 8
+            for (int u = 0; u < span; ++u)
+                if (window_key(t0 + u) < best.kth) cand |= 1u << u;
             while (__ballot_sync(0xffffffffu, cand != 0)) {
                 if (cand) {
                     const int u = __ffs(cand) - 1;
                     cand &= cand - 1;
-                    const int64_t pos = window_pos(t0 + u);
-                    const float4 q = __ldg(&a.pts[pos]);
-                    const uint64_t nk = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
-                                                 __float_as_uint(q.w));
+                    const uint64_t nk = window_key(t0 + u);
                     if (nk < best.kth) best.insert(nk);
                 }
             }
         }
+        __syncwarp();
     }
 
-    int queued = 0;  // entries in this lane's queue
-    auto drain = [&]() {
-        __syncwarp();
-        int e = 0;
-        uint32_t base = 0, cand = 0;
-        while (__ballot_sync(0xffffffffu, cand != 0 || e < queued)) {
-            if (cand == 0 && e < queued) {
-                const uint2 entry = queue[warp][e++][lane];
-                base = entry.x;
-                cand = entry.y;
-            }
-            if (cand) {
-                const int t = __ffs(cand) - 1;
-                cand &= cand - 1;
-                const float4 q = __ldg(&a.pts[base + t]);
-                const uint64_t nk = pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)),
-                                             __float_as_uint(q.w));
-                if (nk < best.kth) best.insert(nk);
-            }
-        }
-        queued = 0;
-        __syncwarp();
-    };
-
     bool guard_ok = true;
-    int sp = 1;
-    if (lane == 0) stk[0] = 0;
-    __syncwarp();
+    int sp = 0;
+    {
+        const NodeBox rb = a.nodes[0];
+        const int32_t rc = a.child[0];
+        const unsigned int need = __ballot_sync(0xffffffffu, active && box_lower_bound(rb, c.x, c.y, c.z) <= best.kth_d2());
+        if (need) {
+            if (lane == 0)
+                stack_e[warp][0] = make_int4(rc, __float_as_int(rb.lo.w), __float_as_int(rb.hi.w), static_cast<int>(need));
+            sp = 1;
+        }
+        __syncwarp();
+    }
     for (int64_t steps = 0; sp > 0; ++steps) {
         if (steps >= a.max_steps) {
             guard_ok = false;
             break;
         }
         --sp;
-        const int32_t node = stk[sp];
+        const int4 e = stack_e[warp][sp];
         __syncwarp();
-        const NodeBox b = a.nodes[node];
-        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
-        const bool need = active && box_lower_bound(b, c.x, c.y, c.z) <= best.kth_d2();
-        if (!__ballot_sync(0xffffffffu, need)) continue;
-        const int32_t fc = a.child[node];
+        const int32_t fc = e.x;
+        const uint32_t start = static_cast<uint32_t>(e.y), end = static_cast<uint32_t>(e.z);
+        const bool need = (static_cast<uint32_t>(e.w) >> lane) & 1u;
         if (fc >= 0) {
             // the largest k-th distance of the group bounds what any lane still needs
             float mkd = active ? best.kth_d2() : -INFINITY;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mkd = fmaxf(mkd, __shfl_xor_sync(0xffffffffu, mkd, o));
             // reachable children, nearest to the group centre first (bitonic sort, lanes 0..7)
+            NodeBox cb;
+            int32_t cc = -1;
             uint64_t key = ~0ull;
             if (lane < 8) {
-                const NodeBox cb = a.nodes[fc + lane];
+                cb = a.nodes[fc + lane];
+                cc = a.child[fc + lane];
                 if (group_lower_bound(cb, glx, gly, glz, ghx, ghy, ghz) <= mkd)
                     key = child_order_key(cb, gx, gy, gz, static_cast<int>(lane));
             }
@@ -374,33 +366,50 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
                     if (lane < 8 && take) key = other;
                 }
             }
-            const bool valid = lane < 8 && (key >> 32) != 0xffffffffull;
-            const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-            if (sp + nvalid <= kStackDepth) {
-                if (valid) stk[sp + nvalid - 1 - static_cast<int>(lane)] = fc + static_cast<int32_t>(key & 7ull);
-                sp += nvalid;
-            } else {
-                guard_ok = false;
+            const int nvalid = __popc(__ballot_sync(0xffffffffu, lane < 8 && (key >> 32) != 0xffffffffull));
+            // push the farthest first so that the nearest is popped first
+            for (int i = nvalid - 1; i >= 0; --i) {
+                const int ci = static_cast<int>(__shfl_sync(0xffffffffu, key, i) & 7ull);
+                const NodeBox b = shfl_node(cb, ci);
+                const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
+                const unsigned int cneed =
+                    __ballot_sync(0xffffffffu, active && box_lower_bound(b, c.x, c.y, c.z) <= best.kth_d2());
+                if (cneed) {
+                    if (sp < kStackDepth) {
+                        if (lane == 0)
+                            stack_e[warp][sp] = make_int4(bc, __float_as_int(b.lo.w), __float_as_int(b.hi.w),
+                                                          static_cast<int>(cneed));
+                        ++sp;
+                    } else {
+                        guard_ok = false;
+                    }
+                }
             }
             __syncwarp();
         } else {
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
+                if (lane < m) buf[lane] = __ldg(&a.pts[base + lane]);
+                __syncwarp();
                 uint32_t cand = 0;
-#pragma unroll 4
+#pragma unroll 8
                 for (uint32_t t = 0; t < m; ++t) {
-                    const float4 q = __ldg(&a.pts[base + t]);
-                    const float d = sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
                     const bool seen = static_cast<uint64_t>(static_cast<int64_t>(base + t) - win_lo) < win_n;
-                    if (pair_key(d, __float_as_uint(q.w)) < best.kth && !seen) cand |= 1u << t;
+                    if (key_of(buf[t]) < best.kth && !seen) cand |= 1u << t;
                 }
                 if (!need) cand = 0;
-                if (cand) queue[warp][queued++][lane] = make_uint2(base, cand);
-                if (__ballot_sync(0xffffffffu, queued == kQueueCap)) drain();
+                while (__ballot_sync(0xffffffffu, cand != 0)) {
+                    if (cand) {
+                        const int t = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        const uint64_t nk = key_of(buf[t]);
+                        if (nk < best.kth) best.insert(nk);
+                    }
+                }
+                __syncwarp();
             }
         }
     }
-    drain();
     if (active) {
         best.finish();
         best.store(a, row);

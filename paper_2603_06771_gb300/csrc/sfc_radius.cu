@@ -85,12 +85,28 @@ __device__ __forceinline__ float axis_gap(float lo, float hi, float glo, float g
     return fmaxf(fmaxf(__fsub_rn(lo, ghi), __fsub_rn(glo, hi)), 0.0f);
 }
 
+// Broadcast lane src's node box to the warp.
+__device__ __forceinline__ NodeBox shfl_box(const NodeBox& b, int src) {
+    NodeBox o;
+    o.lo = make_float4(__shfl_sync(0xffffffffu, b.lo.x, src), __shfl_sync(0xffffffffu, b.lo.y, src),
+                       __shfl_sync(0xffffffffu, b.lo.z, src), __shfl_sync(0xffffffffu, b.lo.w, src));
+    o.hi = make_float4(__shfl_sync(0xffffffffu, b.hi.x, src), __shfl_sync(0xffffffffu, b.hi.y, src),
+                       __shfl_sync(0xffffffffu, b.hi.z, src), __shfl_sync(0xffffffffu, b.hi.w, src));
+    return o;
+}
+
+// The walk keeps, per pushed node, what its parent's expansion learnt: its first child,
+// its point range and which lanes find it undecided or wholly inside their kernel, so a
+// pop reads shared memory only.  An expansion loads the eight children once (lanes 0-7),
+// drops those no centre of the group can reach, and classifies the rest for every lane.
+// Leaf points are staged in shared memory with one coalesced load per 32-point chunk.
 template <int KERN, bool FILL>
 __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a) {
-    __shared__ int32_t stack[kRadiusWarps][kStackDepth];
+    __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
+    __shared__ uint32_t stack_w[kRadiusWarps][kStackDepth];  // lanes taking the node whole
+    __shared__ float4 chunk[kRadiusWarps][32];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    int32_t* stk = stack[warp];
     const int64_t group = static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp;
     const int64_t first = group * 32;
     if (first >= a.nq) return;  // whole warp
@@ -128,15 +144,14 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
             out += end - start;
         }
     };
-    // the hits of a leaf chunk [base, base + m): lane i's row gets the points of its mask
-    auto take_hits = [&](uint32_t hits, uint32_t base, uint32_t m) {
+    // the hits of a leaf chunk: lane i's row gets the ids (my_id of lane j) of its mask's bits
+    auto take_hits = [&](uint32_t hits, int32_t my_id) {
         count += __popc(hits);
         if (FILL) {
             if (out + __popc(hits) > out_end) {  // never true when the count pass agrees
                 guard_ok = false;
                 hits = 0;
             }
-            const int32_t my_id = lane < m ? static_cast<int32_t>(a.perm[base + lane]) : 0;
             unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
             while (todo) {
                 const int src = __ffs(todo) - 1;
@@ -160,7 +175,8 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
                 if (hd.y & kRangeBit) {
                     take_range(__ballot_sync(0xffffffffu, mask != 0), hd.x, hd.y & ~kRangeBit, mask != 0);
                 } else {
-                    take_hits(mask, hd.x, hd.y);
+                    const int32_t my_id = lane < hd.y ? static_cast<int32_t>(a.perm[hd.x + lane]) : 0;
+                    take_hits(mask, my_id);
                 }
             }
             if (!guard_ok) atomicOr(a.err, kGuardTripped);
@@ -197,69 +213,102 @@ __global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a
         ghz = fmaxf(ghz, __shfl_xor_sync(0xffffffffu, ghz, o));
     }
 
-    int sp = 1;
-    if (lane == 0) stk[0] = 0;
-    __syncwarp();
+    int sp = 0;
+    {
+        const NodeBox rb = a.nodes[0];
+        const int32_t rc = a.child[0];
+        const int cls = active ? classify_box<KERN>(rb, c.x, c.y, c.z, a.r, a.r2, prune) : 0;
+        const unsigned int p = __ballot_sync(0xffffffffu, cls == 1);
+        const unsigned int w = __ballot_sync(0xffffffffu, cls == 2);
+        if (p | w) {
+            if (lane == 0) {
+                stack_e[warp][0] = make_int4(rc, __float_as_int(rb.lo.w), __float_as_int(rb.hi.w), static_cast<int>(p));
+                stack_w[warp][0] = w;
+            }
+            sp = 1;
+        }
+        __syncwarp();
+    }
     for (int64_t steps = 0; sp > 0; ++steps) {
         if (steps >= a.max_steps) {
             guard_ok = false;
             break;
         }
         --sp;
-        const int32_t node = stk[sp];
+        const int4 e = stack_e[warp][sp];
+        const uint32_t wmask = stack_w[warp][sp];
         __syncwarp();
-        const NodeBox b = a.nodes[node];
-        const int32_t fc = a.child[node];
-        const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
+        const int32_t fc = e.x;
+        const uint32_t start = static_cast<uint32_t>(e.y), end = static_cast<uint32_t>(e.z);
+        const bool live = active && end > taken_below;
+        const bool my_partial = live && ((static_cast<uint32_t>(e.w) >> lane) & 1u);
+        const bool my_whole = live && ((wmask >> lane) & 1u);
         if (fc >= 0) {
-            int cls = 0;
-            if (active && end > taken_below) cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
-            const unsigned int partial = __ballot_sync(0xffffffffu, cls == 1);
-            const unsigned int whole = __ballot_sync(0xffffffffu, cls == 2);
+            const unsigned int whole = __ballot_sync(0xffffffffu, my_whole);
+            const unsigned int partial = __ballot_sync(0xffffffffu, my_partial);
             if (whole) {
-                take_range(whole, start, end, cls == 2);
-                if (recording) record(start, kRangeBit | end, cls == 2 ? 0xffffffffu : 0u);
-                if (cls == 2) taken_below = end;
+                take_range(whole, start, end, my_whole);
+                if (recording) record(start, kRangeBit | end, my_whole ? 0xffffffffu : 0u);
+                if (my_whole) taken_below = end;
             }
             if (partial) {
-                // keep the non-empty children that some centre of the group may reach;
-                // the first child ends on top of the stack
+                NodeBox cb;
+                int32_t cc = -1;
                 bool keep = false;
                 if (lane < 8) {
-                    const NodeBox cb = a.nodes[fc + lane];
+                    cb = a.nodes[fc + lane];
+                    cc = a.child[fc + lane];
                     if (__float_as_uint(cb.lo.w) != __float_as_uint(cb.hi.w))
                         keep = kernel_holds<KERN>(axis_gap(cb.lo.x, cb.hi.x, glx, ghx),
                                                   axis_gap(cb.lo.y, cb.hi.y, gly, ghy),
                                                   axis_gap(cb.lo.z, cb.hi.z, glz, ghz), a.r, a.r2);
                 }
-                const unsigned int kept = __ballot_sync(0xffffffffu, keep);
-                const int nk = __popc(kept);
-                if (sp + nk <= kStackDepth) {
-                    if (keep) stk[sp + nk - 1 - __popc(kept & below)] = fc + static_cast<int32_t>(lane);
-                    sp += nk;
-                } else {
-                    guard_ok = false;
+                unsigned int kept = __ballot_sync(0xffffffffu, keep);
+                // push the last child first so that the first child is popped first
+                while (kept) {
+                    const int ci = 31 - __clz(kept);
+                    kept &= ~(1u << ci);
+                    const NodeBox b = shfl_box(cb, ci);
+                    const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
+                    // a lane that found the parent disjoint or took it whole has nothing here
+                    const int cls = my_partial ? classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune) : 0;
+                    const unsigned int cp = __ballot_sync(0xffffffffu, cls == 1);
+                    const unsigned int cw = __ballot_sync(0xffffffffu, cls == 2);
+                    if (cp | cw) {
+                        if (sp < kStackDepth) {
+                            if (lane == 0) {
+                                stack_e[warp][sp] = make_int4(bc, __float_as_int(b.lo.w), __float_as_int(b.hi.w),
+                                                              static_cast<int>(cp));
+                                stack_w[warp][sp] = cw;
+                            }
+                            ++sp;
+                        } else {
+                            guard_ok = false;
+                        }
+                    }
                 }
                 __syncwarp();
             }
         } else {
-            // a leaf: every lane tests every point against its own centre; a lane whose
-            // kernel misses the leaf's box gets no hits (the same monotonicity), so only
-            // the lanes that already took an enclosing range are masked out
-            const bool need = active && end > taken_below;
+            // a leaf: the lanes that reach its box test every point against their own centre
+            const bool need = my_partial || my_whole;
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
+                const float4 mine = lane < m ? __ldg(&a.pts[base + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                chunk[warp][lane] = mine;
+                __syncwarp();
                 uint32_t hits = 0;
-#pragma unroll 4
+#pragma unroll 8
                 for (uint32_t t = 0; t < m; ++t) {
-                    const float4 p = __ldg(&a.pts[base + t]);
+                    const float4 p = chunk[warp][t];
                     const bool in = kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z),
                                                        a.r, a.r2);
                     hits |= static_cast<uint32_t>(in) << t;
                 }
+                __syncwarp();
                 if (!need) hits = 0;
                 if (recording && __ballot_sync(0xffffffffu, hits != 0)) record(base, m, hits);
-                take_hits(hits, base, m);
+                take_hits(hits, static_cast<int32_t>(__float_as_uint(mine.w)));
             }
         }
     }
