@@ -32,7 +32,7 @@ WORKLOAD = {
                    "10% buildings, 3 cm jitter)",
     "points": 10_000_000,
     "encoding": "hilbert",
-    "leaf_capacity": 32,
+    "leaf_capacity": 64,
     "radius": {"kernel": "sphere", "r": 2.0},
     "knn_k": 16,
 }

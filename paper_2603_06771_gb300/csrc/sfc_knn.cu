@@ -16,11 +16,13 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "sfc_internal.cuh"
 
 namespace sfc {
 
-constexpr int kKnnWarps = 4;
+constexpr int kKnnWarps = 1;  // one warp per block: per-warp work varies widely
 constexpr uint32_t kNoIndex = 0xffffffffu;
 
 struct KnnArgs {
@@ -210,9 +212,9 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
 }
 
 // resident blocks per SM the register budget is sized for (4 warps each)
-// warps per block of the group kernel: the heaps take KMAX * 256 bytes per warp
+// warps per block of the group kernel
 template <int KMAX>
-__host__ __device__ constexpr int knn_warps() { return KMAX >= 64 ? 2 : kKnnWarps; }
+__host__ __device__ constexpr int knn_warps() { return kKnnWarps; }
 
 __device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
     NodeBox o;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     // skips those positions.
     int64_t win_lo = 0;
     uint32_t win_n = 0;
-    if (a.window > 0) {
+    if (a.window > 0 && 32 + 2 * a.window - 1 <= kBuf) {
         const int64_t r0 = first - (a.window - 1);  // staged positions r0 .. r0 + 95
         for (int j = lane; j < kBuf; j += 32) {
             const int64_t pos = r0 + j;
@@ -296,14 +298,22 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
             return key_of(buf[pos - r0]);
         };
         const int k = a.k;
-        for (int t = 0; t < k; ++t) best.at(t) = window_key(t);
+        const int nfill = min(k, static_cast<int>(2 * a.window));
+        for (int t = 0; t < k; ++t) best.at(t) = t < nfill ? window_key(t) : kNoPair;
         best.heapify();
-        for (int t0 = k; t0 < 2 * a.window; t0 += 32) {
+        for (int t0 = nfill; t0 < 2 * a.window; t0 += 32) {
             const int span = min(32, 2 * static_cast<int>(a.window) - t0);
             uint32_t cand = 0;
+            const float kd = best.kth_d2();
 #pragma unroll 8
-            for (int u = 0; u < span; ++u)
-                if (window_key(t0 + u) < best.kth) cand |= 1u << u;
+            for (int u = 0; u < span; ++u) {
+                const int t = t0 + u;
+                const int64_t pos = p + ((t & 1) ? (t + 1) / 2 : -(t / 2));
+                if (active && pos >= 0 && pos < a.nq) {
+                    const float4 q = buf[pos - r0];
+                    if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << u;
+                }
+            }
             while (__ballot_sync(0xffffffffu, cand != 0)) {
                 if (cand) {
                     const int u = __ffs(cand) - 1;
@@ -391,11 +401,21 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
                 const uint32_t m = min(32u, end - base);
                 if (lane < m) buf[lane] = __ldg(&a.pts[base + lane]);
                 __syncwarp();
+                // pass 1 compares distances only (<= keeps ties for the exact test of pass 2)
+                const float kd = best.kth_d2();
                 uint32_t cand = 0;
 #pragma unroll 8
                 for (uint32_t t = 0; t < m; ++t) {
-                    const bool seen = static_cast<uint64_t>(static_cast<int64_t>(base + t) - win_lo) < win_n;
-                    if (key_of(buf[t]) < best.kth && !seen) cand |= 1u << t;
+                    const float4 q = buf[t];
+                    if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << t;
+                }
+                // positions this lane already saw in its seeding window
+                const int64_t lo = max(win_lo, static_cast<int64_t>(base));
+                const int64_t hi = min(win_lo + static_cast<int64_t>(win_n), static_cast<int64_t>(base) + m);
+                if (lo < hi) {
+                    const uint32_t len = static_cast<uint32_t>(hi - lo);
+                    const uint32_t run = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+                    cand &= ~(run << static_cast<uint32_t>(lo - base));
                 }
                 if (!need) cand = 0;
                 while (__ballot_sync(0xffffffffu, cand != 0)) {
@@ -535,7 +555,9 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.out_d2 = out_d2;
         a.err = &t->scal->bad;
         a.max_steps = t->n_nodes;
-        a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? 32 : 0;
+        // curve neighbours per side for the seeding window: at least k / 2 so that the k
+        // nearest along the curve fill the heap; the staged span 32 + 2 * window - 1 fits 96
+        a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? std::max<int64_t>(16, (k + 1) / 2) : 0;
         if (k <= 8) SFC_TRY(sfc::launch_knn<8>(t, a, s));
         else if (k <= 16) SFC_TRY(sfc::launch_knn<16>(t, a, s));
         else if (k <= 32) SFC_TRY(sfc::launch_knn<32>(t, a, s));

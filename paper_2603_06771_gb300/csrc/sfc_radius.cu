@@ -33,7 +33,9 @@
 
 namespace sfc {
 
-constexpr int kRadiusWarps = 4;
+// warps per block of the group kernel (small blocks: per-warp work varies widely)
+template <bool FILL>
+__host__ __device__ constexpr int radius_warps() { return FILL ? 2 : 1; }
 
 struct RadiusArgs {
     const float4* __restrict__ pts;     // sorted cloud (ordered encodings) or input order (NONE)
@@ -101,7 +103,8 @@ __device__ __forceinline__ NodeBox shfl_box(const NodeBox& b, int src) {
 // drops those no centre of the group can reach, and classifies the rest for every lane.
 // Leaf points are staged in shared memory with one coalesced load per 32-point chunk.
 template <int KERN, bool FILL>
-__global__ void __launch_bounds__(kRadiusWarps * 32) k_radius_group(RadiusArgs a) {
+__global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(RadiusArgs a) {
+    constexpr int kRadiusWarps = radius_warps<FILL>();
     __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
     __shared__ uint32_t stack_w[kRadiusWarps][kStackDepth];  // lanes taking the node whole
     __shared__ float4 chunk[kRadiusWarps][32];
@@ -392,13 +395,14 @@ static sfc_status launch_search(const Octree* t, RadiusArgs& a, int kern, cudaSt
         default: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SQUARE, FILL>), grid, 128, 0, a); break;
         }
     } else {
+        constexpr int kWarps = radius_warps<FILL>();
         const int64_t groups = (a.nq + 31) / 32;
-        const unsigned int grid = grid_for(groups, kRadiusWarps);
+        const unsigned int grid = grid_for(groups, kWarps);
         switch (kern) {
-        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
-        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
-        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
-        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, FILL>), grid, kRadiusWarps * 32, 0, a); break;
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, FILL>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, FILL>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, FILL>), grid, kWarps * 32, 0, a); break;
         }
     }
     return SFC_OK;
