@@ -172,6 +172,53 @@ sfc_status sfc_csr_free(sfc_csr* csr, void* cuda_stream);
 sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_queries, int32_t k, void* cuda_stream,
                int32_t* out_idx, float* out_d2);
 
+/* ---- batched path: many clouds in one pass ------------------------------------------- */
+
+/* What to search in one cloud of a batch: every point of the cloud is a centre. */
+typedef enum { SFC_SEARCH_RADIUS = 0, SFC_SEARCH_KNN = 1 } sfc_search_kind;
+
+typedef struct {
+    int64_t n_points; /* points of this cloud; the clouds are concatenated in the input */
+    int32_t search;   /* sfc_search_kind */
+    int32_t kernel;   /* SFC_SEARCH_RADIUS: sfc_kernel */
+    float r;          /* SFC_SEARCH_RADIUS: radius (r <= 0 gives empty rows) */
+    int32_t k;        /* SFC_SEARCH_KNN: neighbours, 1 <= k <= 64 */
+} sfc_batch_cloud;
+
+typedef struct sfc_batch_s* sfc_batch; /* results of a batch, owned by the library */
+
+/* Build the linear octree of every cloud of a batch and run every cloud's all-points
+ * search, with the same results as octree_build + radius_search / knn on each cloud alone.
+ *   points_xyz  device, sum(n_points) x 3 float32: cloud 0's points, then cloud 1's, ...
+ *   clouds      host array of n_clouds entries (1 <= n_clouds <= 1024).
+ *   enc         SFC_ENC_MORTON or SFC_ENC_HILBERT; opts: NULL for the defaults.
+ * Every step runs once over the whole batch (per-cloud bounding boxes and codes, one radix
+ * sort ordered by (cloud, code), segmented linear-octree kernels, one search launch per
+ * kernel type or kNN size class), so the launch count does not grow with the number of
+ * clouds.  Each cloud gets the pipeline of sections 4 and 5 with its own bounding box,
+ * scale and root; the paper itself processes one cloud per call.  Waits on cuda_stream
+ * three times (node counts, radius output size, the end).  Neighbour indices are
+ * positions inside each cloud.
+ * Errors (then *out = NULL and nothing is held): SFC_ERR_INVALID for a bad argument or
+ * cloud entry (negative n_points, unknown search or kernel, NaN r, k < 1, other
+ * encodings); SFC_ERR_TOO_LARGE for n_clouds > 1024, k > 64, 2^31 - 1 points or more, or
+ * node tables beyond 2^31 entries; SFC_ERR_NOT_DEVICE_PTR; SFC_ERR_NOT_FINITE when any
+ * cloud holds a non-finite coordinate; SFC_ERR_OOM / SFC_ERR_CUDA; SFC_ERR_INTERNAL when
+ * a device guard tripped. */
+sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                        const sfc_build_opts* opts, void* cuda_stream, sfc_batch* out);
+
+/* Device views of one cloud's results (no copy, valid until batch_free):
+ *   radius cloud: row_ptr has n_points + 1 entries whose values index *cols from its start,
+ *                 *nnz = row_ptr[n_points] - row_ptr[0]; knn pointers are NULL.
+ *   kNN cloud:    knn_idx / knn_d2 hold n_points x k entries (layout of knn()); the CSR
+ *                 pointers are NULL and *nnz = 0. */
+sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_ptr, const int32_t** cols,
+                              int64_t* nnz, const int32_t** knn_idx, const float** knn_d2);
+
+/* Release a batch's results (stream ordered on cuda_stream). */
+sfc_status batch_free(sfc_batch b, void* cuda_stream);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------ */
 
 /* Copy the sorted codes (n), the permutation sorted position -> original index (n), the

@@ -16,6 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
+    "Batch", "batch_search",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
 
@@ -72,6 +73,10 @@ _SIGNATURES = {
     "octree_export_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     "sfc_encode_cells": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "batch_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
+    "batch_free": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sfc_status_string": (C.c_char_p, [C.c_int]),
     "sfc_last_error": (C.c_char_p, []),
     "sfc_launch_count": (C.c_uint64, []),
@@ -312,3 +317,79 @@ def profile_read() -> dict:
         name = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         out[name] = (int(launches[i]), float(ms[i]))
     return out
+
+
+# ----------------------------------------------------------------------------- batched path
+class _BatchCloud(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("search", C.c_int32), ("kernel", C.c_int32), ("r", C.c_float),
+                ("k", C.c_int32)]
+
+
+class Batch:
+    """Results of ``batch_search`` (library-owned device memory, released by :meth:`free`)."""
+
+    def __init__(self, handle: C.c_void_p, clouds: list, stream):
+        self._h = handle
+        self._stream = stream
+        self.clouds = clouds
+
+    def _views(self, i: int):
+        rp, cols, knn_i, knn_d = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        nnz = C.c_int64()
+        _check(lib().batch_cloud_result(self._h, int(i), C.byref(rp), C.byref(cols), C.byref(nnz), C.byref(knn_i),
+                                        C.byref(knn_d)), "batch_cloud_result")
+        return rp.value, cols.value, int(nnz.value), knn_i.value, knn_d.value
+
+    def radius(self, i: int):
+        """(row_ptr, cols) of radius cloud i, row_ptr rebased to start at 0 (torch tensors)."""
+        if self._h is None:
+            raise RuntimeError("batch already freed")
+        rp, cols, nnz, _, _ = self._views(i)
+        n = self.clouds[i]["n"]
+        row_ptr = torch.as_tensor(_DeviceArray(self, rp, n + 1, "<i8"), device="cuda")
+        first = int(row_ptr[0].item())
+        col = torch.as_tensor(_DeviceArray(self, cols + 4 * first, nnz, "<i4"), device="cuda")
+        return row_ptr - first, col
+
+    def knn(self, i: int):
+        """(idx [n, k], d2 [n, k]) of kNN cloud i (torch tensors)."""
+        if self._h is None:
+            raise RuntimeError("batch already freed")
+        _, _, _, ki, kd = self._views(i)
+        n, k = self.clouds[i]["n"], self.clouds[i]["k"]
+        idx = torch.as_tensor(_DeviceArray(self, ki, n * k, "<i4"), device="cuda").view(n, k)
+        d2 = torch.as_tensor(_DeviceArray(self, kd, n * k, "<f4"), device="cuda").view(n, k)
+        return idx, d2
+
+    def free(self, stream=None):
+        if self._h is not None:
+            _check(lib().batch_free(self._h, C.c_void_p(_stream(stream))), "batch_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None:
+                lib().batch_free(self._h, C.c_void_p(_stream(self._stream)))
+                self._h = None
+        except Exception:
+            pass
+
+
+def batch_search(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_capacity: int = 32, prune: bool = True,
+                 stream=None) -> Batch:
+    """``batch_search`` of the C ABI.  ``clouds``: list of dicts with ``n`` (points, in order
+    of the concatenated ``points``), ``search`` ("radius" or "knn"), and ``kernel`` / ``r``
+    or ``k``."""
+    pts = _xyz(points, "points")
+    if sum(int(c["n"]) for c in clouds) != pts.shape[0]:
+        raise ValueError("the clouds' sizes must add up to the number of points")
+    arr = (_BatchCloud * len(clouds))()
+    for i, c in enumerate(clouds):
+        radius = c.get("search", "radius") == "radius"
+        arr[i] = _BatchCloud(int(c["n"]), 0 if radius else 1, _kern(c.get("kernel", "sphere")) if radius else 0,
+                             float(c.get("r", 0.0)), int(c.get("k", 0)))
+    opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
+    h = C.c_void_p()
+    _check(lib().batch_search(_ptr(pts), C.byref(arr), len(clouds), _enc(encoding), C.byref(opts),
+                              C.c_void_p(_stream(stream)), C.byref(h)), "batch_search")
+    return Batch(h, [dict(c) for c in clouds], stream)

@@ -85,85 +85,6 @@ __global__ void k_bbox_finish(BuildScalars* sc) {
 }
 
 // ---------------------------------------------------------------------------------
-// section 4.1: Morton code, bits of x, y, z interleaved x-high per level.  Each 21-bit
-// coordinate is spread to every third bit by shift-and-mask steps.
-__device__ __forceinline__ uint64_t spread_every_third(uint32_t v) {
-    uint64_t x = v & kCellMax;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-
-__device__ __forceinline__ uint64_t morton_code(uint32_t x, uint32_t y, uint32_t z) {
-    return (spread_every_third(x) << 2) | (spread_every_third(y) << 1) | spread_every_third(z);
-}
-
-// section 4.2: Hilbert code as a finite-state machine read level by level from the top.
-// The state is the transform that the levels above impose on the remaining bits (a
-// permutation of the three axes with a flip per axis, 48 possibilities) plus the running
-// parity of the code's last bit column (2): 96 states x 8 inputs.  At a level the input
-// bits are transformed by the state, the output digit is the Gray code of the transformed
-// bits complemented when the parity is odd, and the transform of the lower levels then
-// applies, for axes 0, 1, 2 in turn, "complement axis 0" when that axis's transformed bit
-// is 1 and "exchange axis 0 with that axis" when it is 0 (the curve of J. Skilling,
-// "Programming the Hilbert curve", 2004).  Every block fills the table in shared memory.
-constexpr int kHilbertStates = 96;
-constexpr int kHilbertTable = kHilbertStates * 8;
-
-__device__ __forceinline__ void axes_of_perm(int p, int s[3]) {
-    // p = 2 * first + (1 if the other two are descending)
-    s[0] = p >> 1;
-    const int a = s[0] == 0 ? 1 : 0;
-    const int b = s[0] == 2 ? 1 : 2;
-    if (p & 1) { s[1] = b; s[2] = a; }
-    else { s[1] = a; s[2] = b; }
-}
-
-__device__ __forceinline__ int perm_of_axes(const int s[3]) { return 2 * s[0] + (s[1] > s[2] ? 1 : 0); }
-
-__device__ void fill_hilbert_table(uint16_t* table) {
-    for (int t = threadIdx.x; t < kHilbertTable; t += blockDim.x) {
-        const int input = t & 7;
-        const int state = t >> 3;
-        const int parity = state & 1;
-        const int flips = (state >> 1) & 7;
-        int src[3], flip[3], v[3];
-        axes_of_perm(state >> 4, src);
-        for (int i = 0; i < 3; ++i) flip[i] = (flips >> (2 - i)) & 1;
-        const int bits[3] = {(input >> 2) & 1, (input >> 1) & 1, input & 1};
-        for (int i = 0; i < 3; ++i) v[i] = bits[src[i]] ^ flip[i];
-        const int g0 = v[0], g1 = v[0] ^ v[1], g2 = v[0] ^ v[1] ^ v[2];
-        const int digit = ((g0 ^ parity) << 2) | ((g1 ^ parity) << 1) | (g2 ^ parity);
-        const int next_parity = parity ^ g2;
-        for (int i = 0; i < 3; ++i) {
-            if (v[i]) {
-                flip[0] ^= 1;
-            } else {
-                int ts = src[0]; src[0] = src[i]; src[i] = ts;
-                int tf = flip[0]; flip[0] = flip[i]; flip[i] = tf;
-            }
-        }
-        const int next = ((perm_of_axes(src) * 8 + ((flip[0] << 2) | (flip[1] << 1) | flip[2])) << 1) | next_parity;
-        table[t] = static_cast<uint16_t>(digit | (next << 3));
-    }
-}
-
-__device__ __forceinline__ uint64_t hilbert_code(uint32_t x, uint32_t y, uint32_t z, const uint16_t* table) {
-    uint32_t state = 0;
-    uint64_t code = 0;
-#pragma unroll
-    for (int l = kLevels - 1; l >= 0; --l) {
-        const uint32_t in = (((x >> l) & 1u) << 2) | (((y >> l) & 1u) << 1) | ((z >> l) & 1u);
-        const uint32_t e = table[state * 8 + in];
-        code = (code << 3) | (e & 7u);
-        state = e >> 3;
-    }
-    return code;
-}
-
 template <int ENC>
 __global__ void __launch_bounds__(256) k_encode(const float* __restrict__ xyz, int64_t n,
                                                 const BuildScalars* __restrict__ sc, uint64_t* __restrict__ keys,
@@ -197,6 +118,43 @@ __global__ void __launch_bounds__(256) k_encode_cells(const uint32_t* __restrict
         const uint32_t cx = cells[3 * i] & kCellMax, cy = cells[3 * i + 1] & kCellMax, cz = cells[3 * i + 2] & kCellMax;
         keys[i] = ENC == SFC_ENC_HILBERT ? hilbert_code(cx, cy, cz, table) : morton_code(cx, cy, cz);
     }
+}
+
+// codes of a batch: each point takes the box and scale of its cloud
+template <int ENC>
+__global__ void __launch_bounds__(256) k_batch_encode(const float* __restrict__ xyz, int64_t n,
+                                                      const BatchSeg* __restrict__ segs, int nsegs,
+                                                      uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+    __shared__ uint16_t table[kHilbertTable];
+    __shared__ int64_t p0s[kBatchMax];
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_table(table);
+    for (int i = threadIdx.x; i < nsegs; i += blockDim.x) p0s[i] = segs[i].p0;
+    __syncthreads();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = nsegs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p0s[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchSeg& g = segs[lo];
+        const uint32_t cx = cell_of(xyz[3 * i], g.lo[0], g.scale);
+        const uint32_t cy = cell_of(xyz[3 * i + 1], g.lo[1], g.scale);
+        const uint32_t cz = cell_of(xyz[3 * i + 2], g.lo[2], g.scale);
+        keys[i] = ENC == SFC_ENC_HILBERT ? hilbert_code(cx, cy, cz, table) : morton_code(cx, cy, cz);
+        idx[i] = static_cast<uint32_t>(i);
+    }
+}
+
+sfc_status batch_encode(const float* xyz, int64_t n, int enc, const BatchSeg* segs, int nsegs, uint64_t* keys,
+                        uint32_t* idx, cudaStream_t s) {
+    const unsigned int grid = grid_for(n, 256, 152 * 16);
+    if (enc == SFC_ENC_HILBERT)
+        SFC_LAUNCH("batch_encode", s, k_batch_encode<SFC_ENC_HILBERT>, grid, 256, 0, xyz, n, segs, nsegs, keys, idx);
+    else
+        SFC_LAUNCH("batch_encode", s, k_batch_encode<SFC_ENC_MORTON>, grid, 256, 0, xyz, n, segs, nsegs, keys, idx);
+    return SFC_OK;
 }
 
 // ---------------------------------------------------------------------------------

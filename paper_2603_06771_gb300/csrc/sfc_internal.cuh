@@ -85,6 +85,28 @@ struct Octree {
 
 void release_records(Octree* t, cudaStream_t s);
 
+// One cloud of a batched search (see sfc_batch.cu): the group kernels take a table of
+// these; without one they search the single cloud of a handle (root node 0, all rows).
+struct SearchSeg {
+    int64_t group0;  // first warp group (global index) of this cloud
+    int64_t q0, nq;  // its centres: sorted positions [q0, q0 + nq) of the batch
+    int64_t row0;    // radius: its first CSR row; kNN: its first output entry
+    int32_t root;    // its root node
+    int32_t k;       // kNN: neighbours
+    float r, r2;     // radius and fl(r * r)
+};
+
+// Index of the cloud that owns warp group `group` (the last entry with group0 <= group).
+__device__ __forceinline__ int find_search_seg(const SearchSeg* segs, int n, int64_t group) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].group0 <= group) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------------
 // runtime (sfc_runtime.cu)
 void record_cuda_error(cudaError_t e, const char* where);
@@ -259,6 +281,109 @@ __device__ __forceinline__ float sq_dist(float dx, float dy, float dz) {
     float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     return __fadd_rn(s, __fmul_rn(dz, dz));
 }
+
+// ---------------------------------------------------------------------------------
+// section 4.1: Morton code, bits of x, y, z interleaved x-high per level.  Each 21-bit
+// coordinate is spread to every third bit by shift-and-mask steps.
+__device__ __forceinline__ uint64_t spread_every_third(uint32_t v) {
+    uint64_t x = v & kCellMax;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint64_t morton_code(uint32_t x, uint32_t y, uint32_t z) {
+    return (spread_every_third(x) << 2) | (spread_every_third(y) << 1) | spread_every_third(z);
+}
+
+// section 4.2: Hilbert code as a finite-state machine read level by level from the top.
+// The state is the transform that the levels above impose on the remaining bits (a
+// permutation of the three axes with a flip per axis, 48 possibilities) plus the running
+// parity of the code's last bit column (2): 96 states x 8 inputs.  At a level the input
+// bits are transformed by the state, the output digit is the Gray code of the transformed
+// bits complemented when the parity is odd, and the transform of the lower levels then
+// applies, for axes 0, 1, 2 in turn, "complement axis 0" when that axis's transformed bit
+// is 1 and "exchange axis 0 with that axis" when it is 0 (the curve of J. Skilling,
+// "Programming the Hilbert curve", 2004).  Every block fills the table in shared memory.
+constexpr int kHilbertStates = 96;
+constexpr int kHilbertTable = kHilbertStates * 8;
+
+__device__ __forceinline__ void axes_of_perm(int p, int s[3]) {
+    // p = 2 * first + (1 if the other two are descending)
+    s[0] = p >> 1;
+    const int a = s[0] == 0 ? 1 : 0;
+    const int b = s[0] == 2 ? 1 : 2;
+    if (p & 1) { s[1] = b; s[2] = a; }
+    else { s[1] = a; s[2] = b; }
+}
+
+__device__ __forceinline__ int perm_of_axes(const int s[3]) { return 2 * s[0] + (s[1] > s[2] ? 1 : 0); }
+
+__device__ inline void fill_hilbert_table(uint16_t* table) {
+    for (int t = threadIdx.x; t < kHilbertTable; t += blockDim.x) {
+        const int input = t & 7;
+        const int state = t >> 3;
+        const int parity = state & 1;
+        const int flips = (state >> 1) & 7;
+        int src[3], flip[3], v[3];
+        axes_of_perm(state >> 4, src);
+        for (int i = 0; i < 3; ++i) flip[i] = (flips >> (2 - i)) & 1;
+        const int bits[3] = {(input >> 2) & 1, (input >> 1) & 1, input & 1};
+        for (int i = 0; i < 3; ++i) v[i] = bits[src[i]] ^ flip[i];
+        const int g0 = v[0], g1 = v[0] ^ v[1], g2 = v[0] ^ v[1] ^ v[2];
+        const int digit = ((g0 ^ parity) << 2) | ((g1 ^ parity) << 1) | (g2 ^ parity);
+        const int next_parity = parity ^ g2;
+        for (int i = 0; i < 3; ++i) {
+            if (v[i]) {
+                flip[0] ^= 1;
+            } else {
+                int ts = src[0]; src[0] = src[i]; src[i] = ts;
+                int tf = flip[0]; flip[0] = flip[i]; flip[i] = tf;
+            }
+        }
+        const int next = ((perm_of_axes(src) * 8 + ((flip[0] << 2) | (flip[1] << 1) | flip[2])) << 1) | next_parity;
+        table[t] = static_cast<uint16_t>(digit | (next << 3));
+    }
+}
+
+__device__ __forceinline__ uint64_t hilbert_code(uint32_t x, uint32_t y, uint32_t z, const uint16_t* table) {
+    uint32_t state = 0;
+    uint64_t code = 0;
+#pragma unroll
+    for (int l = kLevels - 1; l >= 0; --l) {
+        const uint32_t in = (((x >> l) & 1u) << 2) | (((y >> l) & 1u) << 1) | ((z >> l) & 1u);
+        const uint32_t e = table[state * 8 + in];
+        code = (code << 3) | (e & 7u);
+        state = e >> 3;
+    }
+    return code;
+}
+
+
+// One cloud of a batch (see sfc_batch.cu).
+struct BatchSeg {
+    int64_t p0, n;       // its points: input and sorted positions [p0, p0 + n)
+    int64_t g0, n_int;   // its internal nodes: global pre-order ranks [g0, g0 + n_int)
+    int64_t node0;       // its node-table slice: [node0, node0 + 1 + 8 n_int)
+    int64_t leaf0;       // its leaves slice: [leaf0, leaf0 + 7 n_int + 2)
+    int32_t ncap;
+    int32_t pad;
+    float lo[3];
+    float scale;
+    unsigned int mn[3], mx[3];
+    unsigned int bad;
+};
+constexpr int kBatchMax = 1024;  // clouds per batch (segment starts are staged in shared memory)
+
+// codes of a batch, each cloud with its own box and scale (sfc_build.cu)
+sfc_status batch_encode(const float* xyz, int64_t n, int enc, const BatchSeg* segs, int nsegs, uint64_t* keys,
+                        uint32_t* idx, cudaStream_t s);
+// LSD radix sort on bits [begin_bit, end_bit) of the keys; the result ends in keys / vals
+sfc_status radix_sort_pairs_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                                 int begin_bit, int end_bit, cudaStream_t s, Scratch& scratch);
 
 }  // namespace sfc
 

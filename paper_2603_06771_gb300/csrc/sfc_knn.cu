@@ -15,6 +15,7 @@
 // lane walks alone.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -38,6 +39,10 @@ struct KnnArgs {
     unsigned int* err;
     int64_t max_steps;
     int64_t window;   // > 0: seed each warp's lists from this many curve neighbours on each side
+    // batched search: nsegs clouds, ngroups warp groups in all (segs == nullptr: one cloud)
+    const SearchSeg* segs;
+    int nsegs;
+    int64_t ngroups;
 };
 
 __device__ __forceinline__ float box_lower_bound(const NodeBox& b, float cx, float cy, float cz) {
@@ -153,8 +158,7 @@ struct LaneHeap {
         }
     }
     __device__ __forceinline__ float kth_d2() const { return __uint_as_float(static_cast<uint32_t>(kth >> 32)); }
-    __device__ __forceinline__ void store(const KnnArgs& a, uint32_t row) const {
-        const int64_t base = static_cast<int64_t>(row) * a.k;
+    __device__ __forceinline__ void store(const KnnArgs& a, int64_t base) const {
         for (int s = 0; s < k; ++s) {
             const uint64_t key = at(s);
             const uint32_t id = static_cast<uint32_t>(key);
@@ -240,12 +244,27 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     __shared__ float4 pbuf[kWarps][kBuf];
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    const int64_t first = (static_cast<int64_t>(blockIdx.x) * kWarps + warp) * 32;
-    if (first >= a.nq) return;
+    const int64_t group = static_cast<int64_t>(blockIdx.x) * kWarps + warp;
+    int64_t first = group * 32, q_lo = 0, q_end = a.nq, out0 = 0;
+    int32_t root = 0;
+    int k = a.k;
+    if (a.segs) {
+        if (group >= a.ngroups) return;
+        const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
+        first = sg.q0 + (group - sg.group0) * 32;
+        q_lo = sg.q0;
+        q_end = sg.q0 + sg.nq;
+        out0 = sg.row0;
+        root = sg.root;
+        k = sg.k;
+    } else if (first >= a.nq) {
+        return;
+    }
     const int64_t qi = first + lane;
-    const bool active = qi < a.nq;
+    const bool active = qi < q_end;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t row = __float_as_uint(c.w);
+    // first output entry of this lane's row
+    const int64_t out_base = out0 + static_cast<int64_t>(__float_as_uint(c.w)) * k;
     float4* buf = pbuf[warp];
 
     // centre (orders the walk) and bounding box (prunes it) of the group's centres
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     gx *= inv; gy *= inv; gz *= inv;
 
     LaneHeap best;
-    best.init(&heaps[warp][0][lane], a.k);
+    best.init(&heaps[warp][0][lane], k);
     auto key_of = [&](const float4& q) {
         return pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)), __float_as_uint(q.w));
     };
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
         const int64_t r0 = first - (a.window - 1);  // staged positions r0 .. r0 + 95
         for (int j = lane; j < kBuf; j += 32) {
             const int64_t pos = r0 + j;
-            buf[j] = (pos >= 0 && pos < a.nq) ? __ldg(&a.pts[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            buf[j] = (pos >= q_lo && pos < q_end) ? __ldg(&a.pts[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
         const int64_t p = qi;
@@ -294,10 +313,9 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
         win_n = static_cast<uint32_t>(2 * a.window);
         auto window_key = [&](int t) -> uint64_t {
             const int64_t pos = p + ((t & 1) ? (t + 1) / 2 : -(t / 2));
-            if (!active || pos < 0 || pos >= a.nq) return kNoPair;
+            if (!active || pos < q_lo || pos >= q_end) return kNoPair;
             return key_of(buf[pos - r0]);
         };
-        const int k = a.k;
         const int nfill = min(k, static_cast<int>(2 * a.window));
         for (int t = 0; t < k; ++t) best.at(t) = t < nfill ? window_key(t) : kNoPair;
         best.heapify();
@@ -309,7 +327,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
             for (int u = 0; u < span; ++u) {
                 const int t = t0 + u;
                 const int64_t pos = p + ((t & 1) ? (t + 1) / 2 : -(t / 2));
-                if (active && pos >= 0 && pos < a.nq) {
+                if (active && pos >= q_lo && pos < q_end) {
                     const float4 q = buf[pos - r0];
                     if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << u;
                 }
@@ -329,8 +347,8 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     bool guard_ok = true;
     int sp = 0;
     {
-        const NodeBox rb = a.nodes[0];
-        const int32_t rc = a.child[0];
+        const NodeBox rb = a.nodes[root];
+        const int32_t rc = a.child[root];
         const unsigned int need = __ballot_sync(0xffffffffu, active && box_lower_bound(rb, c.x, c.y, c.z) <= best.kth_d2());
         if (need) {
             if (lane == 0)
@@ -432,7 +450,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     }
     if (active) {
         best.finish();
-        best.store(a, row);
+        best.store(a, out_base);
     }
     if (!guard_ok && lane == 0) atomicOr(a.err, kGuardTripped);
 }
@@ -497,7 +515,39 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
         SFC_LAUNCH("knn", s, k_knn_lane<KMAX>, grid_for(a.nq, 128), 128, 0, a);
     } else {
         constexpr int kWarps = knn_warps<KMAX>();
-        SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for((a.nq + 31) / 32, kWarps), kWarps * 32, 0, a);
+        SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
+    }
+    return SFC_OK;
+}
+
+// all kNN clouds of one list-size class of a batch, in one launch (sfc_batch.cu)
+sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
+                            int32_t* out_idx, float* out_d2, unsigned int* err, cudaStream_t s) {
+    if (ngroups == 0) return SFC_OK;
+    KnnArgs a;
+    memset(&a, 0, sizeof a);
+    a.pts = pts;
+    a.perm = perm;
+    a.nodes = nodes;
+    a.child = child;
+    a.q = pts;
+    a.nq = ngroups * 32;
+    a.k = kmax;
+    a.out_idx = out_idx;
+    a.out_d2 = out_d2;
+    a.err = err;
+    a.max_steps = total_nodes;
+    a.window = window;
+    a.segs = segs;
+    a.nsegs = nsegs;
+    a.ngroups = ngroups;
+    const unsigned int grid = grid_for(ngroups, kKnnWarps);
+    switch (kmax) {
+    case 8: SFC_LAUNCH("batch_knn", s, k_knn_group<8>, grid, kKnnWarps * 32, 0, a); break;
+    case 16: SFC_LAUNCH("batch_knn", s, k_knn_group<16>, grid, kKnnWarps * 32, 0, a); break;
+    case 32: SFC_LAUNCH("batch_knn", s, k_knn_group<32>, grid, kKnnWarps * 32, 0, a); break;
+    default: SFC_LAUNCH("batch_knn", s, k_knn_group<64>, grid, kKnnWarps * 32, 0, a); break;
     }
     return SFC_OK;
 }
@@ -555,6 +605,9 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.out_d2 = out_d2;
         a.err = &t->scal->bad;
         a.max_steps = t->n_nodes;
+        a.segs = nullptr;
+        a.nsegs = 0;
+        a.ngroups = (rows + 31) / 32;
         // curve neighbours per side for the seeding window: at least k / 2 so that the k
         // nearest along the curve fill the heap; the staged span 32 + 2 * window - 1 fits 96
         a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? std::max<int64_t>(16, (k + 1) / 2) : 0;

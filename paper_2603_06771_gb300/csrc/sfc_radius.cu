@@ -57,6 +57,10 @@ struct RadiusArgs {
     uint32_t* rec_masks;
     uint2* rec_head;
     uint32_t* rec_count;
+    // batched search: nsegs clouds, ngroups warp groups in all (segs == nullptr: one cloud)
+    const SearchSeg* segs;
+    int nsegs;
+    int64_t ngroups;
 };
 
 // A record header is (chunk start, chunk size <= 32) for a leaf chunk, or
@@ -111,12 +115,25 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const int64_t group = static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp;
-    const int64_t first = group * 32;
-    if (first >= a.nq) return;  // whole warp
+    int64_t first = group * 32, q_end = a.nq, row0 = 0;
+    int32_t root = 0;
+    float r = a.r, r2 = a.r2;
+    if (a.segs) {
+        if (group >= a.ngroups) return;  // whole warp
+        const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
+        first = sg.q0 + (group - sg.group0) * 32;
+        q_end = sg.q0 + sg.nq;
+        row0 = sg.row0;
+        root = sg.root;
+        r = sg.r;
+        r2 = sg.r2;
+    } else if (first >= a.nq) {
+        return;  // whole warp
+    }
     const int64_t qi = first + lane;
-    const bool active = qi < a.nq;
+    const bool active = qi < q_end;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t row = __float_as_uint(c.w);
+    const int64_t row = row0 + __float_as_uint(c.w);
     const unsigned int below = lanes_below();
     const bool prune = a.prune != 0;
     uint32_t count = 0;
@@ -218,9 +235,9 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
 
     int sp = 0;
     {
-        const NodeBox rb = a.nodes[0];
-        const int32_t rc = a.child[0];
-        const int cls = active ? classify_box<KERN>(rb, c.x, c.y, c.z, a.r, a.r2, prune) : 0;
+        const NodeBox rb = a.nodes[root];
+        const int32_t rc = a.child[root];
+        const int cls = active ? classify_box<KERN>(rb, c.x, c.y, c.z, r, r2, prune) : 0;
         const unsigned int p = __ballot_sync(0xffffffffu, cls == 1);
         const unsigned int w = __ballot_sync(0xffffffffu, cls == 2);
         if (p | w) {
@@ -264,7 +281,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
                     if (__float_as_uint(cb.lo.w) != __float_as_uint(cb.hi.w))
                         keep = kernel_holds<KERN>(axis_gap(cb.lo.x, cb.hi.x, glx, ghx),
                                                   axis_gap(cb.lo.y, cb.hi.y, gly, ghy),
-                                                  axis_gap(cb.lo.z, cb.hi.z, glz, ghz), a.r, a.r2);
+                                                  axis_gap(cb.lo.z, cb.hi.z, glz, ghz), r, r2);
                 }
                 unsigned int kept = __ballot_sync(0xffffffffu, keep);
                 // push the last child first so that the first child is popped first
@@ -274,7 +291,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
                     const NodeBox b = shfl_box(cb, ci);
                     const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
                     // a lane that found the parent disjoint or took it whole has nothing here
-                    const int cls = my_partial ? classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune) : 0;
+                    const int cls = my_partial ? classify_box<KERN>(b, c.x, c.y, c.z, r, r2, prune) : 0;
                     const unsigned int cp = __ballot_sync(0xffffffffu, cls == 1);
                     const unsigned int cw = __ballot_sync(0xffffffffu, cls == 2);
                     if (cp | cw) {
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
                 for (uint32_t t = 0; t < m; ++t) {
                     const float4 p = chunk[warp][t];
                     const bool in = kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z),
-                                                       a.r, a.r2);
+                                                       r, r2);
                     hits |= static_cast<uint32_t>(in) << t;
                 }
                 __syncwarp();
@@ -396,7 +413,7 @@ static sfc_status launch_search(const Octree* t, RadiusArgs& a, int kern, cudaSt
         }
     } else {
         constexpr int kWarps = radius_warps<FILL>();
-        const int64_t groups = (a.nq + 31) / 32;
+        const int64_t groups = a.ngroups;
         const unsigned int grid = grid_for(groups, kWarps);
         switch (kern) {
         case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL>), grid, kWarps * 32, 0, a); break;
@@ -429,6 +446,9 @@ static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, flo
     a.rec_masks = nullptr;
     a.rec_head = nullptr;
     a.rec_count = nullptr;
+    a.segs = nullptr;
+    a.nsegs = 0;
+    a.ngroups = (rows + 31) / 32;
     return a;
 }
 
@@ -565,6 +585,52 @@ static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, c
         SFC_CUDA(cudaMemsetAsync(*bad, 0, sizeof(unsigned int), s));
     }
     return prepare_queries(t, queries, rows, s, scratch, q4, *bad);
+}
+
+// all radius clouds of one kernel type of a batch, in one launch (sfc_batch.cu)
+sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
+                               int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
+                               bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
+                               int prune, cudaStream_t s) {
+    if (ngroups == 0) return SFC_OK;
+    RadiusArgs a;
+    memset(&a, 0, sizeof a);
+    a.pts = pts;
+    a.perm = perm;
+    a.nodes = nodes;
+    a.child = child;
+    a.q = pts;
+    a.nq = ngroups * 32;
+    a.prune = prune;
+    a.counts = counts;
+    a.row_ptr = row_ptr;
+    a.cols = cols;
+    a.err = err;
+    a.max_steps = total_nodes;
+    a.segs = segs;
+    a.nsegs = nsegs;
+    a.ngroups = ngroups;
+    const char* name = fill ? "batch_radius_fill" : "batch_radius_count";
+    if (fill) {
+        constexpr int kWarps = radius_warps<true>();
+        const unsigned int grid = grid_for(ngroups, kWarps);
+        switch (kern) {
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, true>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, true>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, true>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, true>), grid, kWarps * 32, 0, a); break;
+        }
+    } else {
+        constexpr int kWarps = radius_warps<false>();
+        const unsigned int grid = grid_for(ngroups, kWarps);
+        switch (kern) {
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, false>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, false>), grid, kWarps * 32, 0, a); break;
+        }
+    }
+    return SFC_OK;
 }
 
 void release_records(Octree* t, cudaStream_t s) {

@@ -348,9 +348,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
     }
 }
 
-sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                            cudaStream_t s, Scratch& scratch) {
-    if (n <= 1) return SFC_OK;
+sfc_status radix_sort_pairs_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                                 int begin_bit, int end_bit, cudaStream_t s, Scratch& scratch) {
+    if (n <= 1 || end_bit <= begin_bit) return SFC_OK;
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     uint32_t* hist = nullptr;
     SFC_TRY(scratch.alloc(&hist, static_cast<size_t>(kRadix * tiles + 1)));
@@ -358,7 +358,7 @@ sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
     uint32_t* vsrc = vals;
     uint64_t* kdst = keys_alt;
     uint32_t* vdst = vals_alt;
-    for (int shift = 0; shift < 64; shift += kRadixBits) {
+    for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
         SFC_LAUNCH("radix_histogram", s, k_radix_histogram, static_cast<unsigned int>(tiles), kSortThreads, 0, ksrc,
                    n, shift, hist, tiles);
         SFC_TRY(scan_u32_to_u32(hist, hist, kRadix * tiles, s, scratch));
@@ -367,8 +367,16 @@ sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
         uint64_t* tk = ksrc; ksrc = kdst; kdst = tk;
         uint32_t* tv = vsrc; vsrc = vdst; vdst = tv;
     }
-    // an even number of passes leaves the result in keys / vals
+    if (ksrc != keys) {  // an odd number of passes: bring the result back
+        SFC_CUDA(cudaMemcpyAsync(keys, ksrc, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        SFC_CUDA(cudaMemcpyAsync(vals, vsrc, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
     return SFC_OK;
+}
+
+sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                            cudaStream_t s, Scratch& scratch) {
+    return radix_sort_pairs_bits(keys, vals, keys_alt, vals_alt, n, 0, 64, s, scratch);
 }
 
 }  // namespace sfc
