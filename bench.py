@@ -8,6 +8,12 @@ per step).  With --gpus N (launched by torchrun) every rank runs its own replica
 workload (weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--workload batch256 times the batched path instead: 256 clouds of uneven sizes
+(log-uniform 10k-2M points, uniform / LiDAR / Gaussian clusters), each with an
+all-points sphere or kNN search, answered by one batch_search per step, next to the
+plain per-cloud path (octree_build + radius search or kNN, cloud after cloud on one
+stream) on the same clouds.
 """
 from __future__ import annotations
 
@@ -62,6 +68,8 @@ def parse_args(argv=None):
     ap.add_argument("--k", type=int, default=WORKLOAD["knn_k"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256"], default="lidar_tile_10M")
+    ap.add_argument("--clouds", type=int, default=256, help="batch256: number of clouds (testing)")
     return ap.parse_args(argv)
 
 
@@ -251,9 +259,138 @@ def reference_arm(args, cfg):
     return 0
 
 
+# ----------------------------------------------------------------------------- batched workload
+BATCH_METRIC = "batched queries/s on 1 GB300 (256 uneven clouds: build + all-points sphere or kNN per cloud)"
+BATCH_NNZ_CAP = 1 << 28   # neighbours per radius cloud; above it the radius is redrawn smaller
+
+
+def batch_setup(sfc, torch, n_clouds: int, ncap: int, enc: str):
+    """The clouds, concatenated on the device, and their searches.  A radius cloud whose
+    neighbour count exceeds BATCH_NNZ_CAP takes the next smaller radius of the set (counted
+    once here with the plain path, before anything is timed)."""
+    import synth
+
+    specs = synth.batch_workload(n_clouds)
+    xyz = [synth.batch_cloud(sp) for sp in specs]
+    pts = torch.from_numpy(np.concatenate(xyz)).cuda()
+    views, p0, redrawn = [], 0, 0
+    for sp in specs:
+        views.append(pts[p0:p0 + sp["n"]])
+        p0 += sp["n"]
+    for sp, v in zip(specs, views):
+        if sp["search"] != "radius":
+            continue
+        t = sfc.octree_build(v, enc, leaf_capacity=ncap)
+        while True:
+            _, nnz = sfc.radius_count(t, None, sp["r"], sp["kernel"])
+            smaller = [r for r in synth.BATCH_RADII if r < sp["r"]]
+            if nnz <= BATCH_NNZ_CAP or not smaller:
+                break
+            sp["r"] = smaller[-1]
+            redrawn += 1
+        sp["nnz"] = nnz
+        t.free()
+    return specs, pts, views, redrawn
+
+
+def plain_step(sfc, specs, views, enc: str, ncap: int):
+    """Every cloud through the single-cloud entry points, one after the other."""
+    for sp, v in zip(specs, views):
+        t = sfc.octree_build(v, enc, leaf_capacity=ncap)
+        if sp["search"] == "radius":
+            sfc.radius_search(t, None, sp["r"], sp["kernel"])
+        else:
+            sfc.knn(t, None, sp["k"])
+        t.free()
+
+
+def batch_main(args):
+    import torch
+
+    import paper_2603_06771_gb300 as sfc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    sfc.build()
+    enc = args.encoding
+    ncap = args.leaf_capacity
+    specs, pts, views, redrawn = batch_setup(sfc, torch, args.clouds, ncap, enc)
+    n_total = int(pts.shape[0])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clouds = [dict(n=sp["n"], search=sp["search"], kernel=sp.get("kernel", "sphere"), r=sp.get("r", 0.0),
+                   k=sp.get("k", 0)) for sp in specs]
+
+    def timed(fn, steps, warmup):
+        for w in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for s in range(steps):
+            flush.fill_(s)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    def batch_fn():
+        sfc.batch_search(pts, clouds, enc, leaf_capacity=ncap).free()
+
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = sfc.launch_count()
+    b_ms = timed(batch_fn, args.steps, args.warmup)
+    launches = (sfc.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
+    p_ms = timed(lambda: plain_step(sfc, specs, views, enc, ncap), args.steps, args.warmup)
+    clk = clocks.stop()
+    # per-kernel device time of one more step of each path (events around every launch)
+    breakdown = {}
+    for name, fn in (("batch", batch_fn), ("plain", lambda: plain_step(sfc, specs, views, enc, ncap))):
+        torch.cuda.synchronize()
+        sfc.profile_read()
+        sfc.profile_enable(True)
+        fn()
+        torch.cuda.synchronize()
+        sfc.profile_enable(False)
+        breakdown[name] = {k: round(ms, 3) for k, (c, ms) in sorted(sfc.profile_read().items(),
+                                                                     key=lambda kv: -kv[1][1])}
+    b_total, units = aggregate(sum(b_ms), float(n_total * args.steps), world, torch.device("cuda", local))
+    p_total, _ = aggregate(sum(p_ms), float(n_total * args.steps), world, torch.device("cuda", local))
+    if rank == 0:
+        n_radius = sum(sp["search"] == "radius" for sp in specs)
+        line = {
+            "metric": BATCH_METRIC, "value": units / (b_total / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": b_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256", "clouds": len(specs), "points": n_total, "encoding": enc,
+                       "leaf_capacity": ncap, "radius_clouds": n_radius, "knn_clouds": len(specs) - n_radius,
+                       "radius_redrawn": redrawn, "nnz_cap_per_cloud": BATCH_NNZ_CAP,
+                       "nnz": int(sum(sp.get("nnz", 0) for sp in specs)),
+                       "l2": "flushed before every timed step (512 MiB write)"},
+            "plain": {"value": units / (p_total / 1e3), "ms_per_step": p_total / args.steps},
+            "speedup_vs_plain": p_total / b_total,
+            "gpu_launches": launches, "clocks": clk, "kernel_ms": breakdown,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "batch256" and args.impl == "ours":
+        return batch_main(args)
     cfg = dict(WORKLOAD, leaf_capacity=args.leaf_capacity, encoding=args.encoding, knn_k=args.k,
                radius={"kernel": args.kernel, "r": args.radius})
     if args.impl == "reference":

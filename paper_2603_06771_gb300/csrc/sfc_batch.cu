@@ -368,7 +368,7 @@ namespace sfc {
 sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
                                int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
                                bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
-                               int prune, cudaStream_t s);
+                               int prune, const BatchRecords& rec, cudaStream_t s);
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
                             int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
                             int32_t* out_idx, float* out_d2, unsigned int* err, cudaStream_t s);
@@ -542,10 +542,45 @@ static sfc_status run_batch(sfc_batch_s* B, const float* xyz, sfc_encoding enc, 
     SFC_TRY(dev_alloc(&B->row_ptr, n + 1, s));
     SFC_TRY(scratch.alloc(&counts, n));
     SFC_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s));
+    // hit-mask records of the count pass, replayed by the fill; each kernel type's launch
+    // gets its slice.  Without memory for them the fill walks the trees again.
+    int64_t rec_groups = 0;
+    for (int kern = 0; kern < 4; ++kern) rec_groups += radius_groups[kern];
+    BatchRecords rec_all;
+    if (rec_groups > 0) {
+        const int64_t slots = rec_groups * kRecordCap;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&rec_all.masks), sizeof(uint32_t) * 32 * slots, s) !=
+                cudaSuccess ||
+            cudaMallocAsync(reinterpret_cast<void**>(&rec_all.head), sizeof(uint2) * slots, s) != cudaSuccess ||
+            cudaMallocAsync(reinterpret_cast<void**>(&rec_all.count), sizeof(uint32_t) * rec_groups, s) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            dev_free(rec_all.masks, s);
+            dev_free(rec_all.head, s);
+            dev_free(rec_all.count, s);
+            rec_all = BatchRecords();
+        }
+    }
+    struct RecGuard {
+        BatchRecords& r;
+        cudaStream_t s;
+        ~RecGuard() {
+            dev_free(r.masks, s);
+            dev_free(r.head, s);
+            dev_free(r.count, s);
+        }
+    } rec_guard{rec_all, s};
+    BatchRecords rec_of[4];
+    for (int64_t kern = 0, g = 0; kern < 4; g += radius_groups[kern], ++kern) {
+        if (!rec_all.masks) continue;
+        rec_of[kern].masks = rec_all.masks + g * kRecordCap * 32;
+        rec_of[kern].head = rec_all.head + g * kRecordCap;
+        rec_of[kern].count = rec_all.count + g;
+    }
     for (int kern = 0; kern < 4; ++kern)
         SFC_TRY(batch_radius_launch(pts, perm, nodes, child, total_nodes, dsearch + radius_off[kern],
                                     static_cast<int>(radius_sets[kern].size()), radius_groups[kern], kern, false,
-                                    counts, nullptr, nullptr, err, o.prune, s));
+                                    counts, nullptr, nullptr, err, o.prune, rec_of[kern], s));
     SFC_TRY(scan_u32_to_i64(counts, B->row_ptr, n, s, scratch));
     SFC_CUDA(cudaMemcpyAsync(&B->nnz, B->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
@@ -553,7 +588,7 @@ static sfc_status run_batch(sfc_batch_s* B, const float* xyz, sfc_encoding enc, 
     for (int kern = 0; kern < 4; ++kern)
         SFC_TRY(batch_radius_launch(pts, perm, nodes, child, total_nodes, dsearch + radius_off[kern],
                                     static_cast<int>(radius_sets[kern].size()), radius_groups[kern], kern, true,
-                                    counts, B->row_ptr, B->cols, err, o.prune, s));
+                                    counts, B->row_ptr, B->cols, err, o.prune, rec_of[kern], s));
     // per-cloud row bounds and the guard word
     SFC_LAUNCH("batch_row_bounds", s, k_batch_row_bounds, grid_for(static_cast<int64_t>(where.size()), 128), 128, 0,
                B->row_ptr, dwhere, static_cast<int>(where.size()), dbounds);

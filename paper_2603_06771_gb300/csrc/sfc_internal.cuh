@@ -60,6 +60,14 @@ struct RadiusRecords {
     bool valid = false;
 };
 constexpr uint32_t kRecordsOverflow = 0xffffffffu;
+constexpr int kRecordCap = 32;  // record slots per warp of 32 centres (more: the fill walks again)
+
+// The records of one batched radius launch: [groups][kRecordCap] slots (null: no records)
+struct BatchRecords {
+    uint32_t* masks = nullptr;
+    uint2* head = nullptr;
+    uint32_t* count = nullptr;
+};
 
 struct Octree {
     int device = 0;
@@ -245,6 +253,7 @@ __device__ __forceinline__ float ordered_to_float(unsigned int u) {
 }
 
 __device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
+
 __device__ __forceinline__ unsigned int lanes_below() {
     unsigned int m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -470,9 +470,6 @@ static sfc_status check_radius_args(sfc_octree h, const float* queries, int64_t 
     return SFC_OK;
 }
 
-// record slots per warp of 32 centres (a warp that needs more walks again in the fill)
-constexpr int kRecordCap = 32;
-
 // Allocate the hit-mask records of an all-points count pass (ordered encodings only);
 // without memory for them the fill pass simply walks the tree again.
 static void setup_records(Octree* t, int64_t rows, float r, int kern, cudaStream_t s, RadiusArgs& a) {
@@ -591,7 +588,7 @@ static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, c
 sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
                                int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
                                bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
-                               int prune, cudaStream_t s) {
+                               int prune, const BatchRecords& rec, cudaStream_t s) {
     if (ngroups == 0) return SFC_OK;
     RadiusArgs a;
     memset(&a, 0, sizeof a);
@@ -610,6 +607,13 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
     a.segs = segs;
     a.nsegs = nsegs;
     a.ngroups = ngroups;
+    if (rec.masks) {  // the count pass records hit masks, the fill replays them
+        a.rec_mode = fill ? 2 : 1;
+        a.rec_cap = kRecordCap;
+        a.rec_masks = rec.masks;
+        a.rec_head = rec.head;
+        a.rec_count = rec.count;
+    }
     const char* name = fill ? "batch_radius_fill" : "batch_radius_count";
     if (fill) {
         constexpr int kWarps = radius_warps<true>();

@@ -19,6 +19,9 @@ these generators stand in for them):
   value-noise heightfield (0-40 m), 30 % tree crowns (ellipsoids), 10 % box
   buildings with flat or gable roofs, 3 cm Gaussian jitter, 10 points/m^2.
 * ``gaussian_clusters`` - 64 isotropic Gaussian blobs in a cube.
+* ``batch_workload`` / ``batch_cloud`` - many clouds of uneven sizes (log-uniform),
+  the generator cycling uniform / LiDAR tile / Gaussian clusters, each with a
+  radius or kNN search drawn for it.
 """
 from __future__ import annotations
 
@@ -34,6 +37,8 @@ __all__ = [
     "gaussian_clusters",
     "CONFIG_SEED",
     "config_cloud",
+    "batch_workload",
+    "batch_cloud",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -244,3 +249,44 @@ def config_cloud(config: int, n: int | None = None) -> np.ndarray:
     if config in (2, 3):
         return lidar_tile(10_000_000 if n is None else n, seed)
     raise ValueError(f"no single cloud for workload {config}")
+
+
+BATCH_RADII = (0.5, 1.0, 2.0, 3.0)
+BATCH_KS = (8, 16, 32)
+BATCH_GENERATORS = ("uniform", "lidar", "clusters")
+
+
+def batch_workload(n_clouds: int = 256, seed: int = CONFIG_SEED[4], n_lo: int = 10_000,
+                   n_hi: int = 2_000_000) -> list[dict]:
+    """Specs of a batch of clouds: size log-uniform on [n_lo, n_hi], generator cycling
+    uniform (cube side cbrt(n / 2) m) / LiDAR tile (side sqrt(n / 10) m) / Gaussian
+    clusters (64 centres in the cube of side cbrt(n / 2) m, sigma U(1, 5) m); half the
+    clouds get an all-points sphere search with r from {0.5, 1, 2, 3} m, the other half
+    all-points kNN with k from {8, 16, 32}."""
+    rng = Rng(seed)
+    u = rng.u01(0, n_clouds)
+    sizes = np.exp(np.log(n_lo) + u * (np.log(n_hi) - np.log(n_lo)))
+    radius = rng.u01(1, n_clouds) < 0.5
+    ri = rng.integers(2, n_clouds, len(BATCH_RADII))
+    ki = rng.integers(3, n_clouds, len(BATCH_KS))
+    specs = []
+    for i in range(n_clouds):
+        spec = dict(gen=BATCH_GENERATORS[i % 3], n=int(round(sizes[i])), seed=seed * 1000 + i)
+        if radius[i]:
+            spec.update(search="radius", kernel="sphere", r=BATCH_RADII[int(ri[i])])
+        else:
+            spec.update(search="knn", k=BATCH_KS[int(ki[i])])
+        specs.append(spec)
+    return specs
+
+
+def batch_cloud(spec: dict) -> np.ndarray:
+    """The points of one ``batch_workload`` entry."""
+    n, seed = spec["n"], spec["seed"]
+    if n == 0:
+        return np.zeros((0, 3), np.float32)
+    if spec["gen"] == "uniform":
+        return uniform_cube(n, seed, side=(n / 2.0) ** (1.0 / 3.0))
+    if spec["gen"] == "lidar":
+        return lidar_tile(n, seed, side=math.sqrt(n / 10.0))
+    return gaussian_clusters(n, seed)
