@@ -340,6 +340,14 @@ def batch_main(args):
     def batch_fn():
         sfc.batch_search(pts, clouds, enc, leaf_capacity=ncap).free()
 
+    # the same pass recorded as a CUDA graph (points copied into the plan once, untimed)
+    nnz_total = int(sum(sp.get("nnz", 0) for sp in specs))
+    plan = sfc.BatchPlan(clouds, enc, leaf_capacity=ncap, nnz_capacity=nnz_total + nnz_total // 8 + 1)
+    plan.points.copy_(pts)
+
+    def plan_fn():
+        plan.run()
+
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
@@ -349,11 +357,15 @@ def batch_main(args):
     launches0 = sfc.launch_count()
     b_ms = timed(batch_fn, args.steps, args.warmup)
     launches = (sfc.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
+    launches1 = sfc.launch_count()
+    g_ms = timed(plan_fn, args.steps, args.warmup)
+    plan_launches = (sfc.launch_count() - launches1) * args.steps // (args.steps + args.warmup)
     p_ms = timed(lambda: plain_step(sfc, specs, views, enc, ncap), args.steps, args.warmup)
     clk = clocks.stop()
     # per-kernel device time of one more step of each path (events around every launch)
     breakdown = {}
-    for name, fn in (("batch", batch_fn), ("plain", lambda: plain_step(sfc, specs, views, enc, ncap))):
+    for name, fn in (("batch", batch_fn), ("plan", plan_fn),
+                     ("plain", lambda: plain_step(sfc, specs, views, enc, ncap))):
         torch.cuda.synchronize()
         sfc.profile_read()
         sfc.profile_enable(True)
@@ -363,6 +375,7 @@ def batch_main(args):
         breakdown[name] = {k: round(ms, 3) for k, (c, ms) in sorted(sfc.profile_read().items(),
                                                                      key=lambda kv: -kv[1][1])}
     b_total, units = aggregate(sum(b_ms), float(n_total * args.steps), world, torch.device("cuda", local))
+    g_total, _ = aggregate(sum(g_ms), float(n_total * args.steps), world, torch.device("cuda", local))
     p_total, _ = aggregate(sum(p_ms), float(n_total * args.steps), world, torch.device("cuda", local))
     if rank == 0:
         n_radius = sum(sp["search"] == "radius" for sp in specs)
@@ -377,6 +390,8 @@ def batch_main(args):
                        "l2": "flushed before every timed step (512 MiB write)"},
             "plain": {"value": units / (p_total / 1e3), "ms_per_step": p_total / args.steps},
             "speedup_vs_plain": p_total / b_total,
+            "graph": {"value": units / (g_total / 1e3), "ms_per_step": g_total / args.steps,
+                      "speedup_vs_plain": p_total / g_total, "gpu_launches": plan_launches},
             "gpu_launches": launches, "clocks": clk, "kernel_ms": breakdown,
         }
         print(json.dumps(line), flush=True)

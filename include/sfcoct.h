@@ -219,6 +219,47 @@ sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_pt
 /* Release a batch's results (stream ordered on cuda_stream). */
 sfc_status batch_free(sfc_batch b, void* cuda_stream);
 
+/* ---- batch plans: the batched pass recorded once as a CUDA graph and replayed --------- */
+
+typedef struct sfc_batch_plan_s* sfc_batch_plan; /* owned by the library */
+
+/* Record the batched pass of batch_search for a fixed list of clouds (sizes and searches)
+ * as one CUDA graph over buffers allocated here, once: the input points, every work
+ * array, the node tables (sized by a bound on the internal nodes: the internal nodes of
+ * one level hold disjoint sets of more than leaf_capacity points), hit-mask records and
+ * the outputs (radius output: nnz_capacity entries, 0 = 64 per radius centre).
+ * A run is then one graph launch with no allocation and no host wait; sizes the device
+ * learns (node counts, radius output size) are checked on the device, and a run that
+ * outgrows a capacity skips its searches and is repaired by batch_plan_finish.  Same
+ * arguments, results and errors as batch_search, plus SFC_ERR_INVALID when the clouds
+ * hold no point.  Synchronises cuda_stream once. */
+sfc_status batch_plan_create(const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                             const sfc_build_opts* opts, int64_t nnz_capacity, void* cuda_stream,
+                             sfc_batch_plan* out);
+
+/* The plan's input: device, sum(n_points) x 3 float32, cloud after cloud.  The caller
+ * writes the points there (stream ordered before batch_plan_launch). */
+sfc_status batch_plan_points(sfc_batch_plan p, float** points_xyz);
+
+/* Launch one run on cuda_stream (asynchronous; the results of an earlier run are
+ * overwritten).  Each run must be followed by batch_plan_finish before the next. */
+sfc_status batch_plan_launch(sfc_batch_plan p, void* cuda_stream);
+
+/* Wait for the run and check it.  A radius output larger than its capacity is grown to
+ * the exact size and the fill runs again; node tables that did not fit are regrown and the
+ * run repeated (the graph is recorded again before the next launch in both cases).
+ * Errors: SFC_ERR_INVALID without a launch, SFC_ERR_NOT_FINITE, SFC_ERR_TOO_LARGE,
+ * SFC_ERR_OOM / SFC_ERR_CUDA, SFC_ERR_INTERNAL (a device guard tripped). */
+sfc_status batch_plan_finish(sfc_batch_plan p, void* cuda_stream);
+
+/* Views of one cloud's results after batch_plan_finish, as batch_cloud_result; valid until
+ * the next launch or batch_plan_free. */
+sfc_status batch_plan_result(sfc_batch_plan p, int32_t cloud, const int64_t** row_ptr, const int32_t** cols,
+                             int64_t* nnz, const int32_t** knn_idx, const float** knn_d2);
+
+/* Release the plan (waits for cuda_stream first). */
+sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------ */
 
 /* Copy the sorted codes (n), the permutation sorted position -> original index (n), the

@@ -16,7 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
-    "Batch", "batch_search",
+    "Batch", "batch_search", "BatchPlan",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
 
@@ -77,6 +77,13 @@ _SIGNATURES = {
     "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
     "batch_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "batch_plan_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "batch_plan_points": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "batch_plan_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "batch_plan_finish": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "batch_plan_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "batch_plan_free": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sfc_status_string": (C.c_char_p, [C.c_int]),
     "sfc_last_error": (C.c_char_p, []),
     "sfc_launch_count": (C.c_uint64, []),
@@ -325,8 +332,19 @@ class _BatchCloud(C.Structure):
                 ("k", C.c_int32)]
 
 
+def _cloud_array(clouds: list):
+    arr = (_BatchCloud * len(clouds))()
+    for i, c in enumerate(clouds):
+        radius = c.get("search", "radius") == "radius"
+        arr[i] = _BatchCloud(int(c["n"]), 0 if radius else 1, _kern(c.get("kernel", "sphere")) if radius else 0,
+                             float(c.get("r", 0.0)), int(c.get("k", 0)))
+    return arr
+
+
 class Batch:
     """Results of ``batch_search`` (library-owned device memory, released by :meth:`free`)."""
+
+    _result = "batch_cloud_result"
 
     def __init__(self, handle: C.c_void_p, clouds: list, stream):
         self._h = handle
@@ -336,8 +354,8 @@ class Batch:
     def _views(self, i: int):
         rp, cols, knn_i, knn_d = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
         nnz = C.c_int64()
-        _check(lib().batch_cloud_result(self._h, int(i), C.byref(rp), C.byref(cols), C.byref(nnz), C.byref(knn_i),
-                                        C.byref(knn_d)), "batch_cloud_result")
+        _check(getattr(lib(), self._result)(self._h, int(i), C.byref(rp), C.byref(cols), C.byref(nnz),
+                                            C.byref(knn_i), C.byref(knn_d)), self._result)
         return rp.value, cols.value, int(nnz.value), knn_i.value, knn_d.value
 
     def radius(self, i: int):
@@ -348,6 +366,8 @@ class Batch:
         n = self.clouds[i]["n"]
         row_ptr = torch.as_tensor(_DeviceArray(self, rp, n + 1, "<i8"), device="cuda")
         first = int(row_ptr[0].item())
+        if nnz == 0:  # (the address may lie just past the output array)
+            return row_ptr - first, torch.empty(0, dtype=torch.int32, device="cuda")
         col = torch.as_tensor(_DeviceArray(self, cols + 4 * first, nnz, "<i4"), device="cuda")
         return row_ptr - first, col
 
@@ -357,6 +377,9 @@ class Batch:
             raise RuntimeError("batch already freed")
         _, _, _, ki, kd = self._views(i)
         n, k = self.clouds[i]["n"], self.clouds[i]["k"]
+        if n == 0:
+            return (torch.empty((0, k), dtype=torch.int32, device="cuda"),
+                    torch.empty((0, k), dtype=torch.float32, device="cuda"))
         idx = torch.as_tensor(_DeviceArray(self, ki, n * k, "<i4"), device="cuda").view(n, k)
         d2 = torch.as_tensor(_DeviceArray(self, kd, n * k, "<f4"), device="cuda").view(n, k)
         return idx, d2
@@ -383,13 +406,54 @@ def batch_search(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_ca
     pts = _xyz(points, "points")
     if sum(int(c["n"]) for c in clouds) != pts.shape[0]:
         raise ValueError("the clouds' sizes must add up to the number of points")
-    arr = (_BatchCloud * len(clouds))()
-    for i, c in enumerate(clouds):
-        radius = c.get("search", "radius") == "radius"
-        arr[i] = _BatchCloud(int(c["n"]), 0 if radius else 1, _kern(c.get("kernel", "sphere")) if radius else 0,
-                             float(c.get("r", 0.0)), int(c.get("k", 0)))
+    arr = _cloud_array(clouds)
     opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
     h = C.c_void_p()
     _check(lib().batch_search(_ptr(pts), C.byref(arr), len(clouds), _enc(encoding), C.byref(opts),
                               C.c_void_p(_stream(stream)), C.byref(h)), "batch_search")
     return Batch(h, [dict(c) for c in clouds], stream)
+
+
+class BatchPlan(Batch):
+    """``batch_plan_*`` of the C ABI: the batched pass of a fixed list of clouds recorded
+    once as a CUDA graph.  Write the points into :attr:`points`, then :meth:`run` (or
+    :meth:`launch` + :meth:`finish`); :meth:`radius` / :meth:`knn` view the last run."""
+
+    _result = "batch_plan_result"
+
+    def __init__(self, clouds: list, encoding="hilbert", leaf_capacity: int = 32, prune: bool = True,
+                 nnz_capacity: int = 0, stream=None):
+        arr = _cloud_array(clouds)
+        opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
+        h = C.c_void_p()
+        _check(lib().batch_plan_create(C.byref(arr), len(clouds), _enc(encoding), C.byref(opts), int(nnz_capacity),
+                                       C.c_void_p(_stream(stream)), C.byref(h)), "batch_plan_create")
+        super().__init__(h, [dict(c) for c in clouds], stream)
+        ptr = C.c_void_p()
+        _check(lib().batch_plan_points(self._h, C.byref(ptr)), "batch_plan_points")
+        n = sum(int(c["n"]) for c in clouds)
+        self.points = torch.as_tensor(_DeviceArray(self, ptr.value, 3 * n, "<f4"), device="cuda").view(n, 3)
+
+    def launch(self, stream=None):
+        _check(lib().batch_plan_launch(self._h, C.c_void_p(_stream(stream))), "batch_plan_launch")
+
+    def finish(self, stream=None):
+        _check(lib().batch_plan_finish(self._h, C.c_void_p(_stream(stream))), "batch_plan_finish")
+
+    def run(self, stream=None):
+        self.launch(stream)
+        self.finish(stream)
+        return self
+
+    def free(self, stream=None):
+        if self._h is not None:
+            _check(lib().batch_plan_free(self._h, C.c_void_p(_stream(stream))), "batch_plan_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None:
+                lib().batch_plan_free(self._h, C.c_void_p(_stream(self._stream)))
+                self._h = None
+        except Exception:
+            pass

@@ -24,6 +24,18 @@
 
 namespace sfc {
 
+// Sizes the device learns during a batch (read by the later kernels, so that nothing
+// waits for the host), and what went wrong.
+struct BatchTotals {
+    int64_t n_int, n_nodes, n_leaves;  // internal nodes, node-table entries, leaves slots
+    int64_t nnz;                       // radius output entries
+    unsigned int flags;                // kOverNodes | kOverCols | kNonFinite
+    unsigned int pad;
+};
+constexpr unsigned int kOverNodes = 1u;  // the node tables exceed their capacity: no tree, no search
+constexpr unsigned int kOverCols = 2u;   // the radius output exceeds its capacity: no fill
+constexpr unsigned int kNonFinite = 4u;  // a cloud holds a non-finite coordinate
+
 // cloud of position p: the last segment with p0 <= p (segments are in position order)
 __device__ __forceinline__ int seg_of_pos(const int64_t* p0s, int n, int64_t p) {
     int lo = 0, hi = n - 1;
@@ -169,13 +181,69 @@ __global__ void k_batch_seg_internal(BatchSeg* segs, int nsegs, const int64_t* _
     segs[i].n_int = first[segs[i].p0 + segs[i].n] - segs[i].g0;
 }
 
+// Every cloud's slices of the node table and the leaves array (exclusive prefix sums over
+// the clouds, one block), the totals, the capacity check, and the root of every search
+// table entry.
+__global__ void __launch_bounds__(1024) k_batch_layout(BatchSeg* segs, int nsegs, int64_t int_cap, int64_t node_cap,
+                                                       int64_t leaf_cap, SearchSeg* table, const int32_t* table_cloud,
+                                                       int ntable, BatchTotals* tot) {
+    __shared__ int64_t sn[1024], sl[1024];
+    const int i = threadIdx.x;
+    const int64_t ni = i < nsegs ? segs[i].n_int : 0;
+    const int64_t vn = i < nsegs ? 1 + 8 * ni : 0;
+    const int64_t vl = i < nsegs ? 7 * ni + 2 : 0;
+    const int bad = __syncthreads_or(i < nsegs && segs[i].bad != 0u);
+    sn[i] = vn;
+    sl[i] = vl;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan (Hillis-Steele)
+        const int64_t an = i >= o ? sn[i - o] : 0;
+        const int64_t al = i >= o ? sl[i - o] : 0;
+        __syncthreads();
+        sn[i] += an;
+        sl[i] += al;
+        __syncthreads();
+    }
+    if (i < nsegs) {
+        segs[i].node0 = sn[i] - vn;
+        segs[i].leaf0 = sl[i] - vl;
+    }
+    if (i == 1023) {
+        const int64_t nodes = sn[1023], leaves = sl[1023];
+        const int64_t internal = (nodes - nsegs) / 8;
+        unsigned int f = bad ? kNonFinite : 0u;
+        if (internal > int_cap || nodes > node_cap || leaves > leaf_cap || nodes > 0x7fffffffLL) f |= kOverNodes;
+        tot->n_int = internal;
+        tot->n_nodes = nodes;
+        tot->n_leaves = leaves;
+        tot->nnz = 0;
+        tot->flags = f;
+    }
+    __syncthreads();
+    for (int j = i; j < ntable; j += 1024) table[j].root = static_cast<int32_t>(segs[table_cloud[j]].node0);
+}
+
+// child links start as "leaf", arrival counters at zero (over the sizes of this run)
+__global__ void __launch_bounds__(256) k_batch_tree_init(int32_t* __restrict__ child, unsigned int* __restrict__ arrive,
+                                                         const BatchTotals* tot) {
+    if (tot->flags & kOverNodes) return;
+    const int64_t nodes = tot->n_nodes, internal = tot->n_int;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < nodes; s += stride) {
+        child[s] = -1;
+        if (s < internal) arrive[s] = 0u;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_batch_tree_emit(const uint64_t* __restrict__ keys, int64_t n,
                                                          const BatchSeg* segs, int nsegs,
                                                          const uint32_t* __restrict__ cnt,
                                                          const int64_t* __restrict__ first,
-                                                         uint64_t* __restrict__ ikey, uint8_t* __restrict__ ilevel) {
+                                                         uint64_t* __restrict__ ikey, uint8_t* __restrict__ ilevel,
+                                                         const BatchTotals* tot) {
     __shared__ int64_t p0s[kBatchMax];
     load_p0(segs, nsegs, p0s);
+    if (tot->flags & kOverNodes) return;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride) {
         const uint32_t c = cnt[j];
@@ -215,9 +283,10 @@ __device__ __forceinline__ int seg_of_node(const BatchSeg* segs, int n, int64_t 
 }
 
 __global__ void __launch_bounds__(256) k_batch_tree_link(const uint64_t* __restrict__ ikey,
-                                                         const uint8_t* __restrict__ ilevel, int64_t total_int,
+                                                         const uint8_t* __restrict__ ilevel, const BatchTotals* tot,
                                                          const BatchSeg* segs, int nsegs, int32_t* __restrict__ child,
                                                          int32_t* __restrict__ islot) {
+    const int64_t total_int = (tot->flags & kOverNodes) ? 0 : tot->n_int;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total_int; g += stride) {
         const BatchSeg& sg = segs[seg_of_internal(segs, nsegs, g)];
@@ -262,10 +331,11 @@ __device__ __forceinline__ int64_t lower_bound_range(const uint64_t* a, int64_t 
 __global__ void __launch_bounds__(256) k_batch_tree_nodes(const uint64_t* __restrict__ keys,
                                                           const uint64_t* __restrict__ ikey,
                                                           const uint8_t* __restrict__ ilevel, const BatchSeg* segs,
-                                                          int nsegs, int64_t total_nodes,
+                                                          int nsegs, const BatchTotals* tot,
                                                           const int32_t* __restrict__ child, NodeBox* __restrict__ nodes,
                                                           uint64_t* __restrict__ leaves,
                                                           uint32_t* __restrict__ leaf_counts) {
+    const int64_t total_nodes = (tot->flags & kOverNodes) ? 0 : tot->n_nodes;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < total_nodes; s += stride) {
         const BatchSeg& sg = segs[seg_of_node(segs, nsegs, s)];
@@ -301,7 +371,8 @@ __global__ void __launch_bounds__(256) k_batch_tree_nodes(const uint64_t* __rest
 __global__ void __launch_bounds__(256) k_batch_tree_boxes(const float4* __restrict__ pts, const BatchSeg* segs,
                                                           int nsegs, NodeBox* nodes, const int32_t* __restrict__ child,
                                                           const int32_t* __restrict__ islot, unsigned int* arrive,
-                                                          int64_t total_nodes) {
+                                                          const BatchTotals* tot) {
+    const int64_t total_nodes = (tot->flags & kOverNodes) ? 0 : tot->n_nodes;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < total_nodes; s += stride) {
         if (child[s] >= 0) continue;
@@ -337,6 +408,13 @@ __global__ void __launch_bounds__(256) k_batch_tree_boxes(const float4* __restri
     }
 }
 
+// the radius output size against the capacity of the output array
+__global__ void k_batch_check_cols(const int64_t* __restrict__ row_end, int64_t cols_cap, BatchTotals* tot) {
+    const int64_t nnz = *row_end;
+    tot->nnz = nnz;
+    if (nnz > cols_cap) atomicOr(&tot->flags, kOverCols);
+}
+
 __global__ void k_batch_row_bounds(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ where, int n,
                                    int64_t* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,16 +424,326 @@ __global__ void k_batch_row_bounds(const int64_t* __restrict__ row_ptr, const in
 }  // namespace sfc
 
 // ---------------------------------------------------------------------------------
-// the batch handle
-struct sfc_batch_s {
-    int32_t n_clouds = 0;
-    std::vector<sfc_batch_cloud> clouds;
-    std::vector<int64_t> p0;           // first input position of every cloud
-    std::vector<int64_t> out0;         // kNN clouds: first output entry
-    std::vector<int64_t> row_lo, row_hi;  // radius clouds: row_ptr[p0], row_ptr[p0 + n]
+// host side
+
+namespace sfc {
+
+// launches declared in sfc_radius.cu / sfc_knn.cu
+sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
+                               int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
+                               bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
+                               int prune, const BatchRecords& rec, const unsigned int* skip, unsigned int skip_mask,
+                               cudaStream_t s);
+sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
+                            int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
+                            unsigned int skip_mask, cudaStream_t s);
+
+// Internal nodes of a cloud of n points at most: the internal nodes of one level hold
+// disjoint sets of more than ncap points each, and a level l has at most 8^l nodes.
+static int64_t internal_bound(int64_t n, int64_t ncap) {
+    if (n <= ncap) return 0;
+    const int64_t per_level = n / (ncap + 1);
+    int64_t total = 0, level_max = 1;
+    for (int l = 0; l < kLevels; ++l) {
+        total += std::min(level_max, per_level);
+        if (level_max < per_level) level_max *= 8;
+    }
+    return total;
+}
+
+constexpr int kLaunchSets = 8;  // radius kernels 0-3, kNN list sizes 8 / 16 / 32 / 64
+
+// What follows from the clouds' sizes and searches alone.
+struct BatchTables {
+    int n_clouds = 0;
     int64_t n_total = 0;
-    int64_t nnz = 0;
+    std::vector<BatchSeg> seg;         // p0, n, ncap of every cloud
+    std::vector<SearchSeg> table;      // launch tables, one slice per launch (roots set on the device)
+    std::vector<int32_t> table_cloud;  // the cloud of every table entry
+    int64_t off[kLaunchSets], count[kLaunchSets], groups[kLaunchSets];
+    int window[kLaunchSets];
+    std::vector<int64_t> where;  // the row_ptr positions bounding every cloud's rows
+    std::vector<int64_t> out0;   // kNN clouds: first output entry
     int64_t knn_total = 0;
+    int64_t rec_groups = 0;  // warp groups of the radius launches
+    int64_t int_bound = 0;   // internal nodes of all clouds at most
+};
+
+static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, BatchTables& T) {
+    T.n_clouds = n_clouds;
+    T.seg.resize(n_clouds);
+    T.out0.assign(n_clouds, 0);
+    std::vector<SearchSeg> sets[kLaunchSets];
+    std::vector<int32_t> set_cloud[kLaunchSets];
+    int64_t p = 0;
+    for (int i = 0; i < n_clouds; ++i) {
+        const sfc_batch_cloud& c = clouds[i];
+        BatchSeg& g = T.seg[i];
+        memset(&g, 0, sizeof g);
+        g.p0 = p;
+        g.n = c.n_points;
+        g.ncap = ncap;
+        T.int_bound += internal_bound(c.n_points, ncap);
+        T.where.push_back(p);
+        T.where.push_back(p + c.n_points);
+        if (c.n_points > 0) {
+            SearchSeg q;
+            memset(&q, 0, sizeof q);
+            q.q0 = p;
+            q.nq = c.n_points;
+            q.k = c.k;
+            q.r = c.r;
+            q.r2 = c.r * c.r;
+            if (c.search == SFC_SEARCH_RADIUS) {
+                if (c.r > 0.f) {  // r <= 0: every row empty
+                    q.row0 = p;
+                    sets[c.kernel].push_back(q);
+                    set_cloud[c.kernel].push_back(i);
+                }
+            } else {
+                q.row0 = T.knn_total;
+                T.out0[i] = T.knn_total;
+                T.knn_total += c.n_points * c.k;
+                const int b = 4 + (c.k <= 8 ? 0 : (c.k <= 16 ? 1 : (c.k <= 32 ? 2 : 3)));
+                sets[b].push_back(q);
+                set_cloud[b].push_back(i);
+            }
+        }
+        p += c.n_points;
+    }
+    T.n_total = p;
+    for (int t = 0; t < kLaunchSets; ++t) {
+        T.off[t] = static_cast<int64_t>(T.table.size());
+        T.count[t] = static_cast<int64_t>(sets[t].size());
+        int64_t g = 0;
+        int w = 16;  // curve neighbours per side for the kNN seeding window (at least k / 2)
+        for (size_t j = 0; j < sets[t].size(); ++j) {
+            sets[t][j].group0 = g;
+            g += (sets[t][j].nq + 31) / 32;
+            w = std::max(w, (sets[t][j].k + 1) / 2);
+            T.table.push_back(sets[t][j]);
+            T.table_cloud.push_back(set_cloud[t][j]);
+        }
+        T.groups[t] = g;
+        T.window[t] = w;
+        if (t < 4) T.rec_groups += g;
+    }
+}
+
+// The device buffers of one batch run.
+struct BatchBuffers {
+    uint64_t *codes = nullptr, *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *perm = nullptr, *cnt = nullptr, *counts = nullptr;
+    float4* pts = nullptr;
+    int64_t* first = nullptr;
+    BatchSeg* segs = nullptr;
+    SearchSeg* table = nullptr;
+    int32_t* table_cloud = nullptr;
+    int64_t *where = nullptr, *bounds = nullptr;
+    BatchTotals* tot = nullptr;
+    unsigned int* err = nullptr;
+    int64_t int_cap = 0, node_cap = 0, leaf_cap = 0;  // tree capacities
+    NodeBox* nodes = nullptr;
+    int32_t *child = nullptr, *islot = nullptr;
+    uint64_t *ikey = nullptr, *leaves = nullptr;
+    uint8_t* ilevel = nullptr;
+    uint32_t* leaf_counts = nullptr;
+    unsigned int* arrive = nullptr;
+    BatchRecords rec;  // hit-mask records of the radius launches (optional)
+};
+
+// per-point buffers and tables (not the trees, the records or the outputs)
+static sfc_status alloc_base(const BatchTables& T, BatchBuffers& b, Scratch& m) {
+    const int64_t n = T.n_total;
+    SFC_TRY(m.alloc(&b.codes, n));
+    SFC_TRY(m.alloc(&b.k0, n));
+    SFC_TRY(m.alloc(&b.k1, n));
+    SFC_TRY(m.alloc(&b.v0, n));
+    SFC_TRY(m.alloc(&b.v1, n));
+    SFC_TRY(m.alloc(&b.perm, n));
+    SFC_TRY(m.alloc(&b.cnt, n));
+    SFC_TRY(m.alloc(&b.counts, n));
+    SFC_TRY(m.alloc(&b.pts, n));
+    SFC_TRY(m.alloc(&b.first, n + 1));
+    SFC_TRY(m.alloc(&b.segs, T.n_clouds));
+    SFC_TRY(m.alloc(&b.table, T.table.size()));
+    SFC_TRY(m.alloc(&b.table_cloud, T.table.size()));
+    SFC_TRY(m.alloc(&b.where, T.where.size()));
+    SFC_TRY(m.alloc(&b.bounds, T.where.size()));
+    SFC_TRY(m.alloc(&b.tot, 1));
+    SFC_TRY(m.alloc(&b.err, 1));
+    return SFC_OK;
+}
+
+static sfc_status alloc_trees(BatchBuffers& b, Scratch& m) {
+    SFC_TRY(m.alloc(&b.nodes, b.node_cap));
+    SFC_TRY(m.alloc(&b.child, b.node_cap));
+    SFC_TRY(m.alloc(&b.islot, b.int_cap));
+    SFC_TRY(m.alloc(&b.ikey, b.int_cap));
+    SFC_TRY(m.alloc(&b.ilevel, b.int_cap));
+    SFC_TRY(m.alloc(&b.arrive, b.int_cap));
+    SFC_TRY(m.alloc(&b.leaves, b.leaf_cap));
+    SFC_TRY(m.alloc(&b.leaf_counts, b.leaf_cap));
+    return SFC_OK;
+}
+
+// Records for every radius warp group; without the memory the fill walks the trees again.
+static void alloc_records(const BatchTables& T, BatchBuffers& b, Scratch& m) {
+    b.rec = BatchRecords();
+    if (T.rec_groups == 0) return;
+    const int64_t slots = T.rec_groups * kRecordCap;
+    BatchRecords r;
+    if (m.try_alloc(&r.masks, 32 * slots) && m.try_alloc(&r.head, slots) && m.try_alloc(&r.count, T.rec_groups))
+        b.rec = r;
+}
+
+static sfc_status upload_tables(const BatchTables& T, BatchBuffers& b, cudaStream_t s) {
+    SFC_CUDA(cudaMemcpyAsync(b.segs, T.seg.data(), sizeof(BatchSeg) * T.n_clouds, cudaMemcpyHostToDevice, s));
+    if (!T.table.empty()) {
+        SFC_CUDA(cudaMemcpyAsync(b.table, T.table.data(), sizeof(SearchSeg) * T.table.size(), cudaMemcpyHostToDevice,
+                                 s));
+        SFC_CUDA(cudaMemcpyAsync(b.table_cloud, T.table_cloud.data(), sizeof(int32_t) * T.table.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    SFC_CUDA(cudaMemcpyAsync(b.where, T.where.data(), sizeof(int64_t) * T.where.size(), cudaMemcpyHostToDevice, s));
+    return SFC_OK;
+}
+
+// Sections 4 and 5.1 up to the node counts: per-cloud boxes and codes, the (cloud, code)
+// order, the gathered points, the internal nodes of every cloud and the slices they get.
+static sfc_status enqueue_order(const BatchTables& T, BatchBuffers& b, const float* xyz, int enc, cudaStream_t s,
+                                Scratch& tmp) {
+    const int nsegs = T.n_clouds;
+    const int64_t n = T.n_total;
+    const unsigned int sgrid = grid_for(nsegs, 128);
+    const unsigned int grid = grid_for(n, 256, 152 * 16);
+    SFC_CUDA(cudaMemsetAsync(b.err, 0, sizeof(unsigned int), s));
+    SFC_LAUNCH("batch_bbox_init", s, k_bseg_init, sgrid, 128, 0, b.segs, nsegs);
+    SFC_LAUNCH("batch_bbox", s, k_batch_bbox, grid, 256, 0, xyz, n, b.segs, nsegs);
+    SFC_LAUNCH("batch_bbox_finish", s, k_batch_bbox_finish, sgrid, 128, 0, b.segs, nsegs);
+    SFC_TRY(batch_encode(xyz, n, enc, b.segs, nsegs, b.codes, b.v0, s));
+    SFC_CUDA(cudaMemcpyAsync(b.k0, b.codes, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    SFC_TRY(radix_sort_pairs(b.k0, b.v0, b.k1, b.v1, n, s, tmp));
+    if (nsegs > 1) {  // stable pass on the cloud number: order (cloud, code)
+        SFC_LAUNCH("batch_cloud_keys", s, k_batch_cloud_keys, grid, 256, 0, b.v0, n, b.segs, nsegs, b.k0);
+        int bits = 0;
+        while ((1 << bits) < nsegs) ++bits;
+        SFC_TRY(radix_sort_pairs_bits(b.k0, b.v0, b.k1, b.v1, n, 0, bits, s, tmp));
+    }
+    // k1 receives the sorted codes
+    SFC_LAUNCH("batch_gather", s, k_batch_gather, grid, 256, 0, xyz, n, b.codes, b.v0, b.segs, nsegs, b.k1, b.pts,
+               b.perm);
+    SFC_LAUNCH("batch_tree_count", s, k_batch_tree_count, grid, 256, 0, b.k1, n, b.segs, nsegs, b.cnt);
+    SFC_TRY(scan_u32_to_i64(b.cnt, b.first, n, s, tmp));
+    SFC_LAUNCH("batch_seg_internal", s, k_batch_seg_internal, sgrid, 128, 0, b.segs, nsegs, b.first);
+    SFC_LAUNCH("batch_layout", s, k_batch_layout, 1, 1024, 0, b.segs, nsegs, b.int_cap, b.node_cap, b.leaf_cap, b.table,
+               b.table_cloud, static_cast<int>(T.table.size()), b.tot);
+    return SFC_OK;
+}
+
+// Section 5.1: the linear octrees of all clouds (sizes read on the device).
+static sfc_status enqueue_trees(const BatchTables& T, BatchBuffers& b, cudaStream_t s) {
+    const int nsegs = T.n_clouds;
+    const int64_t n = T.n_total;
+    const unsigned int grid = grid_for(n, 256, 152 * 16);
+    const unsigned int igrid = grid_for(std::max<int64_t>(b.int_cap, 1), 256, 152 * 16);
+    const unsigned int ngrid = grid_for(b.node_cap, 256, 152 * 16);
+    SFC_LAUNCH("batch_tree_init", s, k_batch_tree_init, ngrid, 256, 0, b.child, b.arrive, b.tot);
+    SFC_LAUNCH("batch_tree_emit", s, k_batch_tree_emit, grid, 256, 0, b.k1, n, b.segs, nsegs, b.cnt, b.first, b.ikey,
+               b.ilevel, b.tot);
+    SFC_LAUNCH("batch_tree_link", s, k_batch_tree_link, igrid, 256, 0, b.ikey, b.ilevel, b.tot, b.segs, nsegs, b.child,
+               b.islot);
+    SFC_LAUNCH("batch_tree_nodes", s, k_batch_tree_nodes, ngrid, 256, 0, b.k1, b.ikey, b.ilevel, b.segs, nsegs, b.tot,
+               b.child, b.nodes, b.leaves, b.leaf_counts);
+    SFC_LAUNCH("batch_tree_boxes", s, k_batch_tree_boxes, ngrid, 256, 0, b.pts, b.segs, nsegs, b.nodes, b.child,
+               b.islot, b.arrive, b.tot);
+    return SFC_OK;
+}
+
+static BatchRecords records_of(const BatchTables& T, const BatchBuffers& b, int kern) {
+    BatchRecords r;
+    if (!b.rec.masks) return r;
+    int64_t g = 0;
+    for (int t = 0; t < kern; ++t) g += T.groups[t];
+    r.masks = b.rec.masks + g * kRecordCap * 32;
+    r.head = b.rec.head + g * kRecordCap;
+    r.count = b.rec.count + g;
+    return r;
+}
+
+// Section 3.3 for every kNN cloud: one launch per list size.
+static sfc_status enqueue_knn(const BatchTables& T, BatchBuffers& b, int32_t* knn_idx, float* knn_d2, cudaStream_t s) {
+    const int kmax_of[4] = {8, 16, 32, 64};
+    for (int t = 4; t < kLaunchSets; ++t)
+        SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.window[t], knn_idx, knn_d2,
+                                 b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
+    return SFC_OK;
+}
+
+// Section 5.1 neighboursPrune, count pass, then the row pointers.
+static sfc_status enqueue_radius_count(const BatchTables& T, BatchBuffers& b, int prune, int64_t* row_ptr,
+                                       cudaStream_t s, Scratch& tmp) {
+    SFC_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * T.n_total, s));
+    for (int kern = 0; kern < 4; ++kern)
+        SFC_TRY(batch_radius_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[kern],
+                                    static_cast<int>(T.count[kern]), T.groups[kern], kern, false, b.counts, nullptr,
+                                    nullptr, b.err, prune, records_of(T, b, kern), &b.tot->flags, kOverNodes | kNonFinite,
+                                    s));
+    return scan_u32_to_i64(b.counts, row_ptr, T.n_total, s, tmp);
+}
+
+// The fill pass into cols (capacity cols_cap), then every cloud's row bounds.
+static sfc_status enqueue_radius_fill(const BatchTables& T, BatchBuffers& b, int prune, const int64_t* row_ptr,
+                                      int32_t* cols, int64_t cols_cap, cudaStream_t s) {
+    SFC_LAUNCH("batch_check_cols", s, k_batch_check_cols, 1, 1, 0, row_ptr + T.n_total, cols_cap, b.tot);
+    for (int kern = 0; kern < 4; ++kern)
+        SFC_TRY(batch_radius_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[kern],
+                                    static_cast<int>(T.count[kern]), T.groups[kern], kern, true, b.counts, row_ptr,
+                                    cols, b.err, prune, records_of(T, b, kern), &b.tot->flags,
+                                    kOverNodes | kOverCols | kNonFinite, s));
+    SFC_LAUNCH("batch_row_bounds", s, k_batch_row_bounds, grid_for(static_cast<int64_t>(T.where.size()), 128), 128, 0,
+               row_ptr, b.where, static_cast<int>(T.where.size()), b.bounds);
+    return SFC_OK;
+}
+
+static sfc_status check_batch_args(const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                                   const sfc_build_opts* opts, sfc_build_opts* o, int64_t* total) {
+    if (!clouds || n_clouds < 1) return SFC_ERR_INVALID;
+    if (n_clouds > kBatchMax) return SFC_ERR_TOO_LARGE;
+    if (enc != SFC_ENC_MORTON && enc != SFC_ENC_HILBERT) return SFC_ERR_INVALID;
+    sfc_build_opts_default(o);
+    if (opts) *o = *opts;
+    if (o->leaf_capacity < 1 || (o->prune != 0 && o->prune != 1)) return SFC_ERR_INVALID;
+    *total = 0;
+    for (int i = 0; i < n_clouds; ++i) {
+        const sfc_batch_cloud& c = clouds[i];
+        if (c.n_points < 0) return SFC_ERR_INVALID;
+        if (c.search == SFC_SEARCH_RADIUS) {
+            if (c.kernel < 0 || c.kernel > 3 || isnan(c.r)) return SFC_ERR_INVALID;
+        } else if (c.search == SFC_SEARCH_KNN) {
+            if (c.k < 1) return SFC_ERR_INVALID;
+            if (c.k > kMaxK) return SFC_ERR_TOO_LARGE;
+        } else {
+            return SFC_ERR_INVALID;
+        }
+        *total += c.n_points;
+    }
+    if (*total > 0x7fffffffLL - 1) return SFC_ERR_TOO_LARGE;
+    return SFC_OK;
+}
+
+}  // namespace sfc
+
+// ---------------------------------------------------------------------------------
+// batch_search: one pass with exact sizes (the host waits for the node counts and the
+// radius output size)
+struct sfc_batch_s {
+    sfc::BatchTables T;
+    std::vector<sfc_batch_cloud> clouds_;
+    std::vector<int64_t> row_lo, row_hi;  // radius clouds: row_ptr[p0], row_ptr[p0 + n]
+    int64_t nnz = 0;
     int64_t* row_ptr = nullptr;
     int32_t* cols = nullptr;
     int32_t* knn_idx = nullptr;
@@ -364,240 +752,43 @@ struct sfc_batch_s {
 
 namespace sfc {
 
-// launch declared in sfc_radius.cu / sfc_knn.cu
-sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                               int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
-                               bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
-                               int prune, const BatchRecords& rec, cudaStream_t s);
-sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
-                            int32_t* out_idx, float* out_d2, unsigned int* err, cudaStream_t s);
-
-static sfc_status run_batch(sfc_batch_s* B, const float* xyz, sfc_encoding enc, const sfc_build_opts& o,
-                            cudaStream_t s) {
-    Scratch scratch(s);
-    const int nsegs = B->n_clouds;
-    const int64_t n = B->n_total;
-    std::vector<BatchSeg> hseg(nsegs);
-    for (int i = 0; i < nsegs; ++i) {
-        memset(&hseg[i], 0, sizeof(BatchSeg));
-        hseg[i].p0 = B->p0[i];
-        hseg[i].n = B->clouds[i].n_points;
-        hseg[i].ncap = o.leaf_capacity;
-    }
-    BatchSeg* segs = nullptr;
-    SFC_TRY(scratch.alloc(&segs, nsegs));
-    SFC_CUDA(cudaMemcpyAsync(segs, hseg.data(), sizeof(BatchSeg) * nsegs, cudaMemcpyHostToDevice, s));
-    const unsigned int sgrid = grid_for(nsegs, 128);
-    const unsigned int grid = grid_for(n, 256, 152 * 16);
-    SFC_LAUNCH("batch_bbox_init", s, k_bseg_init, sgrid, 128, 0, segs, nsegs);
-    SFC_LAUNCH("batch_bbox", s, k_batch_bbox, grid, 256, 0, xyz, n, segs, nsegs);
-    SFC_LAUNCH("batch_bbox_finish", s, k_batch_bbox_finish, sgrid, 128, 0, segs, nsegs);
-
-    // codes, sort by code, then by cloud (stable): order (cloud, code)
-    uint64_t *codes, *k0, *k1;
-    uint32_t *v0, *v1, *perm;
-    float4* pts;
-    SFC_TRY(scratch.alloc(&codes, n));
-    SFC_TRY(scratch.alloc(&k0, n));
-    SFC_TRY(scratch.alloc(&k1, n));
-    SFC_TRY(scratch.alloc(&v0, n));
-    SFC_TRY(scratch.alloc(&v1, n));
-    SFC_TRY(scratch.alloc(&perm, n));
-    SFC_TRY(scratch.alloc(&pts, n));
-    SFC_TRY(batch_encode(xyz, n, enc, segs, nsegs, codes, v0, s));
-    SFC_CUDA(cudaMemcpyAsync(k0, codes, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
-    SFC_TRY(radix_sort_pairs(k0, v0, k1, v1, n, s, scratch));
-    if (nsegs > 1) {
-        SFC_LAUNCH("batch_cloud_keys", s, k_batch_cloud_keys, grid, 256, 0, v0, n, segs, nsegs, k0);
-        int bits = 0;
-        while ((1 << bits) < nsegs) ++bits;
-        SFC_TRY(radix_sort_pairs_bits(k0, v0, k1, v1, n, 0, bits, s, scratch));
-    }
-    uint64_t* keys = k1;  // the sorted codes
-    SFC_LAUNCH("batch_gather", s, k_batch_gather, grid, 256, 0, xyz, n, codes, v0, segs, nsegs, keys, pts, perm);
-
-    // linear octrees
-    uint32_t* cnt;
-    int64_t* first;
-    SFC_TRY(scratch.alloc(&cnt, n));
-    SFC_TRY(scratch.alloc(&first, n + 1));
-    SFC_LAUNCH("batch_tree_count", s, k_batch_tree_count, grid, 256, 0, keys, n, segs, nsegs, cnt);
-    SFC_TRY(scan_u32_to_i64(cnt, first, n, s, scratch));
-    SFC_LAUNCH("batch_seg_internal", s, k_batch_seg_internal, sgrid, 128, 0, segs, nsegs, first);
-    SFC_CUDA(cudaMemcpyAsync(hseg.data(), segs, sizeof(BatchSeg) * nsegs, cudaMemcpyDeviceToHost, s));
+static sfc_status run_batch(sfc_batch_s* B, const float* xyz, int enc, const sfc_build_opts& o, cudaStream_t s) {
+    const BatchTables& T = B->T;
+    const int64_t n = T.n_total;
+    Scratch tmp(s);
+    BatchBuffers b;
+    b.int_cap = b.node_cap = b.leaf_cap = INT64_MAX;  // sized once the counts are known
+    SFC_TRY(alloc_base(T, b, tmp));
+    SFC_TRY(upload_tables(T, b, s));
+    SFC_TRY(enqueue_order(T, b, xyz, enc, s, tmp));
+    BatchTotals ht;
+    SFC_CUDA(cudaMemcpyAsync(&ht, b.tot, sizeof ht, cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
-    int64_t total_int = 0, total_nodes = 0, total_leaves = 0;
-    for (int i = 0; i < nsegs; ++i) {
-        if (hseg[i].bad) return SFC_ERR_NOT_FINITE;
-        hseg[i].node0 = total_nodes;
-        hseg[i].leaf0 = total_leaves;
-        total_int += hseg[i].n_int;
-        total_nodes += 1 + 8 * hseg[i].n_int;
-        total_leaves += 7 * hseg[i].n_int + 2;
-    }
-    if (total_nodes > 0x7fffffffLL) return SFC_ERR_TOO_LARGE;
-
-    // search tables: radius clouds grouped by kernel, kNN clouds by list size; one launch
-    // per group, each reading its slice of one table.  They go up with the segment table,
-    // while the device is idle, together with the positions whose row_ptr entries bound
-    // every cloud's rows.
-    std::vector<SearchSeg> radius_sets[4], knn_sets[4];
-    int64_t knn_total = 0;
-    for (int i = 0; i < nsegs; ++i) {
-        const sfc_batch_cloud& cl = B->clouds[i];
-        if (cl.n_points == 0) continue;
-        SearchSeg q;
-        memset(&q, 0, sizeof q);
-        q.q0 = hseg[i].p0;
-        q.nq = cl.n_points;
-        q.root = static_cast<int32_t>(hseg[i].node0);
-        q.k = cl.k;
-        q.r = cl.r;
-        q.r2 = cl.r * cl.r;
-        if (cl.search == SFC_SEARCH_RADIUS) {
-            if (!(cl.r > 0.f)) continue;  // r <= 0: every row empty
-            q.row0 = hseg[i].p0;
-            radius_sets[cl.kernel].push_back(q);
-        } else {
-            q.row0 = knn_total;
-            B->out0[i] = knn_total;
-            knn_total += cl.n_points * cl.k;
-            const int bucket = cl.k <= 8 ? 0 : (cl.k <= 16 ? 1 : (cl.k <= 32 ? 2 : 3));
-            knn_sets[bucket].push_back(q);
-        }
-    }
-    std::vector<SearchSeg> table;
-    int64_t radius_off[4], radius_groups[4], knn_off[4], knn_groups[4];
-    auto append = [&](std::vector<SearchSeg>& v, int64_t* off, int64_t* ngroups) {
-        *off = static_cast<int64_t>(table.size());
-        int64_t g = 0;
-        for (auto& q : v) {
-            q.group0 = g;
-            g += (q.nq + 31) / 32;
-            table.push_back(q);
-        }
-        *ngroups = g;
-    };
-    for (int t = 0; t < 4; ++t) append(radius_sets[t], &radius_off[t], &radius_groups[t]);
-    for (int t = 0; t < 4; ++t) append(knn_sets[t], &knn_off[t], &knn_groups[t]);
-    std::vector<int64_t> where;
-    for (int i = 0; i < nsegs; ++i) {
-        where.push_back(hseg[i].p0);
-        where.push_back(hseg[i].p0 + hseg[i].n);
-    }
-    SearchSeg* dsearch = nullptr;
-    int64_t *dwhere, *dbounds;
-    SFC_TRY(scratch.alloc(&dsearch, table.empty() ? 1 : table.size()));
-    SFC_TRY(scratch.alloc(&dwhere, where.size()));
-    SFC_TRY(scratch.alloc(&dbounds, where.size()));
-    SFC_CUDA(cudaMemcpyAsync(segs, hseg.data(), sizeof(BatchSeg) * nsegs, cudaMemcpyHostToDevice, s));
-    if (!table.empty())
-        SFC_CUDA(cudaMemcpyAsync(dsearch, table.data(), sizeof(SearchSeg) * table.size(), cudaMemcpyHostToDevice, s));
-    SFC_CUDA(cudaMemcpyAsync(dwhere, where.data(), sizeof(int64_t) * where.size(), cudaMemcpyHostToDevice, s));
-
-    NodeBox* nodes;
-    int32_t *child, *islot;
-    uint64_t *ikey, *leaves;
-    uint8_t* ilevel;
-    uint32_t* leaf_counts;
-    unsigned int *arrive, *err;
-    SFC_TRY(scratch.alloc(&nodes, total_nodes));
-    SFC_TRY(scratch.alloc(&child, total_nodes));
-    SFC_TRY(scratch.alloc(&islot, total_int));
-    SFC_TRY(scratch.alloc(&ikey, total_int));
-    SFC_TRY(scratch.alloc(&ilevel, total_int));
-    SFC_TRY(scratch.alloc(&arrive, total_int));
-    SFC_TRY(scratch.alloc(&leaves, total_leaves));
-    SFC_TRY(scratch.alloc(&leaf_counts, total_leaves));
-    SFC_TRY(scratch.alloc(&err, 1));
-    SFC_CUDA(cudaMemsetAsync(child, 0xff, sizeof(int32_t) * total_nodes, s));
-    SFC_CUDA(cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * (total_int ? total_int : 1), s));
-    SFC_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned int), s));
-    if (total_int > 0) {
-        SFC_LAUNCH("batch_tree_emit", s, k_batch_tree_emit, grid, 256, 0, keys, n, segs, nsegs, cnt, first, ikey, ilevel);
-        SFC_LAUNCH("batch_tree_link", s, k_batch_tree_link, grid_for(total_int, 256, 152 * 16), 256, 0, ikey, ilevel,
-                   total_int, segs, nsegs, child, islot);
-    }
-    const unsigned int ngrid = grid_for(total_nodes, 256, 152 * 16);
-    SFC_LAUNCH("batch_tree_nodes", s, k_batch_tree_nodes, ngrid, 256, 0, keys, ikey, ilevel, segs, nsegs, total_nodes,
-               child, nodes, leaves, leaf_counts);
-    SFC_LAUNCH("batch_tree_boxes", s, k_batch_tree_boxes, ngrid, 256, 0, pts, segs, nsegs, nodes, child, islot, arrive,
-               total_nodes);
-
+    if (ht.flags & kNonFinite) return SFC_ERR_NOT_FINITE;
+    if (ht.flags & kOverNodes) return SFC_ERR_TOO_LARGE;
+    b.int_cap = ht.n_int;
+    b.node_cap = ht.n_nodes;
+    b.leaf_cap = ht.n_leaves;
+    SFC_TRY(alloc_trees(b, tmp));
+    SFC_TRY(enqueue_trees(T, b, s));
     // kNN first, then the radius count: the device works through both while the host
     // waits for the radius output size
-    B->knn_total = knn_total;
-    SFC_TRY(dev_alloc(&B->knn_idx, knn_total, s));
-    SFC_TRY(dev_alloc(&B->knn_d2, knn_total, s));
-    const int kmax_of[4] = {8, 16, 32, 64};
-    for (int bkt = 0; bkt < 4; ++bkt) {
-        int window = 16;  // curve neighbours per side for the seeding window (at least k / 2)
-        for (auto& q : knn_sets[bkt]) window = std::max(window, (q.k + 1) / 2);
-        SFC_TRY(batch_knn_launch(pts, perm, nodes, child, total_nodes, dsearch + knn_off[bkt],
-                                 static_cast<int>(knn_sets[bkt].size()), knn_groups[bkt], kmax_of[bkt], window,
-                                 B->knn_idx, B->knn_d2, err, s));
-    }
-    uint32_t* counts = nullptr;
+    SFC_TRY(dev_alloc(&B->knn_idx, T.knn_total, s));
+    SFC_TRY(dev_alloc(&B->knn_d2, T.knn_total, s));
+    SFC_TRY(enqueue_knn(T, b, B->knn_idx, B->knn_d2, s));
     SFC_TRY(dev_alloc(&B->row_ptr, n + 1, s));
-    SFC_TRY(scratch.alloc(&counts, n));
-    SFC_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s));
-    // hit-mask records of the count pass, replayed by the fill; each kernel type's launch
-    // gets its slice.  Without memory for them the fill walks the trees again.
-    int64_t rec_groups = 0;
-    for (int kern = 0; kern < 4; ++kern) rec_groups += radius_groups[kern];
-    BatchRecords rec_all;
-    if (rec_groups > 0) {
-        const int64_t slots = rec_groups * kRecordCap;
-        if (cudaMallocAsync(reinterpret_cast<void**>(&rec_all.masks), sizeof(uint32_t) * 32 * slots, s) !=
-                cudaSuccess ||
-            cudaMallocAsync(reinterpret_cast<void**>(&rec_all.head), sizeof(uint2) * slots, s) != cudaSuccess ||
-            cudaMallocAsync(reinterpret_cast<void**>(&rec_all.count), sizeof(uint32_t) * rec_groups, s) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            dev_free(rec_all.masks, s);
-            dev_free(rec_all.head, s);
-            dev_free(rec_all.count, s);
-            rec_all = BatchRecords();
-        }
-    }
-    struct RecGuard {
-        BatchRecords& r;
-        cudaStream_t s;
-        ~RecGuard() {
-            dev_free(r.masks, s);
-            dev_free(r.head, s);
-            dev_free(r.count, s);
-        }
-    } rec_guard{rec_all, s};
-    BatchRecords rec_of[4];
-    for (int64_t kern = 0, g = 0; kern < 4; g += radius_groups[kern], ++kern) {
-        if (!rec_all.masks) continue;
-        rec_of[kern].masks = rec_all.masks + g * kRecordCap * 32;
-        rec_of[kern].head = rec_all.head + g * kRecordCap;
-        rec_of[kern].count = rec_all.count + g;
-    }
-    for (int kern = 0; kern < 4; ++kern)
-        SFC_TRY(batch_radius_launch(pts, perm, nodes, child, total_nodes, dsearch + radius_off[kern],
-                                    static_cast<int>(radius_sets[kern].size()), radius_groups[kern], kern, false,
-                                    counts, nullptr, nullptr, err, o.prune, rec_of[kern], s));
-    SFC_TRY(scan_u32_to_i64(counts, B->row_ptr, n, s, scratch));
+    alloc_records(T, b, tmp);
+    SFC_TRY(enqueue_radius_count(T, b, o.prune, B->row_ptr, s, tmp));
     SFC_CUDA(cudaMemcpyAsync(&B->nnz, B->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
     SFC_TRY(dev_alloc(&B->cols, B->nnz, s));
-    for (int kern = 0; kern < 4; ++kern)
-        SFC_TRY(batch_radius_launch(pts, perm, nodes, child, total_nodes, dsearch + radius_off[kern],
-                                    static_cast<int>(radius_sets[kern].size()), radius_groups[kern], kern, true,
-                                    counts, B->row_ptr, B->cols, err, o.prune, rec_of[kern], s));
-    // per-cloud row bounds and the guard word
-    SFC_LAUNCH("batch_row_bounds", s, k_batch_row_bounds, grid_for(static_cast<int64_t>(where.size()), 128), 128, 0,
-               B->row_ptr, dwhere, static_cast<int>(where.size()), dbounds);
-    std::vector<int64_t> bounds(where.size());
+    SFC_TRY(enqueue_radius_fill(T, b, o.prune, B->row_ptr, B->cols, B->nnz, s));
+    std::vector<int64_t> bounds(T.where.size());
     unsigned int herr = 0;
-    SFC_CUDA(cudaMemcpyAsync(bounds.data(), dbounds, sizeof(int64_t) * bounds.size(), cudaMemcpyDeviceToHost, s));
-    SFC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaMemcpyAsync(bounds.data(), b.bounds, sizeof(int64_t) * bounds.size(), cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < nsegs; ++i) {
+    for (int i = 0; i < T.n_clouds; ++i) {
         B->row_lo[i] = bounds[2 * i];
         B->row_hi[i] = bounds[2 * i + 1];
     }
@@ -616,35 +807,144 @@ static void free_batch(sfc_batch_s* B, cudaStream_t s) {
     B->knn_d2 = nullptr;
 }
 
+// views of one cloud's results (shared by batches and plans)
+static sfc_status cloud_views(const BatchTables& T, int32_t cloud, const int64_t* row_ptr, const int32_t* cols,
+                              const int32_t* knn_idx, const float* knn_d2, const std::vector<int64_t>& row_lo,
+                              const std::vector<int64_t>& row_hi, const int64_t** rp, const int32_t** cl,
+                              int64_t* nnz, const int32_t** ki, const float** kd, const sfc_batch_cloud& c) {
+    const bool radius = c.search == SFC_SEARCH_RADIUS;
+    if (rp) *rp = radius ? row_ptr + T.seg[cloud].p0 : nullptr;
+    if (cl) *cl = radius ? cols : nullptr;
+    if (nnz) *nnz = radius ? row_hi[cloud] - row_lo[cloud] : 0;
+    if (ki) *ki = radius ? nullptr : knn_idx + T.out0[cloud];
+    if (kd) *kd = radius ? nullptr : knn_d2 + T.out0[cloud];
+    return SFC_OK;
+}
+
+}  // namespace sfc
+
+// ---------------------------------------------------------------------------------
+// batch plans: the same pass recorded once as a CUDA graph over buffers sized in advance
+// (trees by the bound on internal nodes, the radius output by a capacity), so that a run
+// is one graph launch with no allocation and no host wait.  Overflows are found on the
+// device (the searches of the run are skipped) and repaired in batch_plan_finish.
+struct sfc_batch_plan_s {
+    sfc::BatchTables T;
+    std::vector<sfc_batch_cloud> clouds;
+    int enc = 0;
+    sfc_build_opts o{};
+    cudaStream_t cs = nullptr;      // capture stream
+    sfc::Scratch* mem = nullptr;    // buffers that live as long as the plan
+    sfc::Scratch* trees = nullptr;  // the tree buffers (replaced when they overflow)
+    sfc::BatchBuffers b;
+    float* xyz = nullptr;
+    int64_t* row_ptr = nullptr;
+    int32_t* cols = nullptr;
+    int64_t cols_cap = 0;
+    int32_t* knn_idx = nullptr;
+    float* knn_d2 = nullptr;
+    struct Status {
+        sfc::BatchTotals tot;
+        unsigned int err;
+        unsigned int pad;
+    }* host = nullptr;              // pinned, written by the graph's last copies
+    int64_t* host_bounds = nullptr; // pinned
+    std::vector<int64_t> row_lo, row_hi;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels_per_run = 0;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+    bool ready = false;  // results of the last run are complete
+};
+
+namespace sfc {
+
+static void release_cols(sfc_batch_plan_s* P) {
+    dev_free(P->cols, P->cs);
+    P->cols = nullptr;
+}
+
+static sfc_status capture_plan(sfc_batch_plan_s* P) {
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    const uint64_t launches0 = sfc_launch_count();
+    cudaGraph_t graph = nullptr;
+    SFC_CUDA(cudaStreamBeginCapture(P->cs, cudaStreamCaptureModeThreadLocal));
+    sfc_status st = SFC_OK;
+    {
+        Scratch tmp(P->cs);  // temporaries of one run (sort and scan work arrays): graph allocations
+        const cudaStream_t s = P->cs;
+        BatchBuffers& b = P->b;
+        st = enqueue_order(P->T, b, P->xyz, P->enc, s, tmp);
+        if (st == SFC_OK) st = enqueue_trees(P->T, b, s);
+        if (st == SFC_OK) st = enqueue_knn(P->T, b, P->knn_idx, P->knn_d2, s);
+        if (st == SFC_OK) st = enqueue_radius_count(P->T, b, P->o.prune, P->row_ptr, s, tmp);
+        if (st == SFC_OK) st = enqueue_radius_fill(P->T, b, P->o.prune, P->row_ptr, P->cols, P->cols_cap, s);
+        if (st == SFC_OK &&
+            (cudaMemcpyAsync(P->host_bounds, b.bounds, sizeof(int64_t) * P->T.where.size(), cudaMemcpyDeviceToHost,
+                             s) != cudaSuccess ||
+             cudaMemcpyAsync(&P->host->tot, b.tot, sizeof(BatchTotals), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+             cudaMemcpyAsync(&P->host->err, b.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess))
+            st = SFC_ERR_CUDA;
+    }
+    const cudaError_t e = cudaStreamEndCapture(P->cs, &graph);
+    P->kernels_per_run = sfc_launch_count() - launches0;
+    if (st != SFC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "cudaStreamEndCapture");
+        if (graph) cudaGraphDestroy(graph);
+        return SFC_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&P->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        record_cuda_error(ie, "cudaGraphInstantiate");
+        P->exec = nullptr;
+        return SFC_ERR_CUDA;
+    }
+    return SFC_OK;
+}
+
+static sfc_status plan_alloc_trees(sfc_batch_plan_s* P, int64_t int_cap) {
+    delete P->trees;
+    P->trees = new (std::nothrow) Scratch(P->cs);
+    if (!P->trees) return SFC_ERR_OOM;
+    P->b.int_cap = int_cap;
+    P->b.node_cap = P->T.n_clouds + 8 * int_cap;
+    P->b.leaf_cap = 2 * P->T.n_clouds + 7 * int_cap;
+    return alloc_trees(P->b, *P->trees);
+}
+
+static void destroy_plan(sfc_batch_plan_s* P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->cs) cudaStreamSynchronize(P->cs);
+    release_cols(P);
+    delete P->trees;
+    delete P->mem;
+    if (P->cs) cudaStreamSynchronize(P->cs);
+    if (P->host) cudaFreeHost(P->host);
+    if (P->host_bounds) cudaFreeHost(P->host_bounds);
+    if (P->done) cudaEventDestroy(P->done);
+    if (P->cs) cudaStreamDestroy(P->cs);
+    delete P;
+}
+
 }  // namespace sfc
 
 extern "C" {
 
 sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
                         const sfc_build_opts* opts, void* cuda_stream, sfc_batch* out) {
-    if (!out || !clouds || n_clouds < 1) return SFC_ERR_INVALID;
+    if (!out) return SFC_ERR_INVALID;
     *out = nullptr;
-    if (n_clouds > sfc::kBatchMax) return SFC_ERR_TOO_LARGE;
-    if (enc != SFC_ENC_MORTON && enc != SFC_ENC_HILBERT) return SFC_ERR_INVALID;
     sfc_build_opts o;
-    sfc_build_opts_default(&o);
-    if (opts) o = *opts;
-    if (o.leaf_capacity < 1 || (o.prune != 0 && o.prune != 1)) return SFC_ERR_INVALID;
     int64_t total = 0;
-    for (int i = 0; i < n_clouds; ++i) {
-        const sfc_batch_cloud& c = clouds[i];
-        if (c.n_points < 0) return SFC_ERR_INVALID;
-        if (c.search == SFC_SEARCH_RADIUS) {
-            if (c.kernel < 0 || c.kernel > 3 || isnan(c.r)) return SFC_ERR_INVALID;
-        } else if (c.search == SFC_SEARCH_KNN) {
-            if (c.k < 1) return SFC_ERR_INVALID;
-            if (c.k > sfc::kMaxK) return SFC_ERR_TOO_LARGE;
-        } else {
-            return SFC_ERR_INVALID;
-        }
-        total += c.n_points;
-    }
-    if (total > 0x7fffffffLL - 1) return SFC_ERR_TOO_LARGE;
+    SFC_TRY(sfc::check_batch_args(clouds, n_clouds, enc, opts, &o, &total));
     if (total > 0 && (!points_xyz || !sfc::is_device_ptr(points_xyz))) return SFC_ERR_NOT_DEVICE_PTR;
     int dev = 0;
     SFC_CUDA(cudaGetDevice(&dev));
@@ -652,18 +952,10 @@ sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     sfc_batch_s* B = new (std::nothrow) sfc_batch_s;
     if (!B) return SFC_ERR_OOM;
-    B->n_clouds = n_clouds;
-    B->clouds.assign(clouds, clouds + n_clouds);
-    B->p0.resize(n_clouds);
-    B->out0.assign(n_clouds, 0);
+    sfc::make_tables(clouds, n_clouds, o.leaf_capacity, B->T);
+    B->clouds_.assign(clouds, clouds + n_clouds);
     B->row_lo.assign(n_clouds, 0);
     B->row_hi.assign(n_clouds, 0);
-    int64_t p = 0;
-    for (int i = 0; i < n_clouds; ++i) {
-        B->p0[i] = p;
-        p += clouds[i].n_points;
-    }
-    B->n_total = total;
     sfc_status st = total > 0 ? sfc::run_batch(B, points_xyz, enc, o, s) : SFC_OK;
     if (st == SFC_OK && total == 0) {
         st = sfc::dev_alloc(&B->row_ptr, 1, s);
@@ -680,20 +972,146 @@ sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, 
 
 sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_ptr, const int32_t** cols, int64_t* nnz,
                               const int32_t** knn_idx, const float** knn_d2) {
-    if (!b || cloud < 0 || cloud >= b->n_clouds) return SFC_ERR_INVALID;
-    const sfc_batch_cloud& c = b->clouds[cloud];
-    if (row_ptr) *row_ptr = c.search == SFC_SEARCH_RADIUS ? b->row_ptr + b->p0[cloud] : nullptr;
-    if (cols) *cols = c.search == SFC_SEARCH_RADIUS ? b->cols : nullptr;
-    if (nnz) *nnz = c.search == SFC_SEARCH_RADIUS ? b->row_hi[cloud] - b->row_lo[cloud] : 0;
-    if (knn_idx) *knn_idx = c.search == SFC_SEARCH_KNN ? b->knn_idx + b->out0[cloud] : nullptr;
-    if (knn_d2) *knn_d2 = c.search == SFC_SEARCH_KNN ? b->knn_d2 + b->out0[cloud] : nullptr;
-    return SFC_OK;
+    if (!b || cloud < 0 || cloud >= b->T.n_clouds) return SFC_ERR_INVALID;
+    return sfc::cloud_views(b->T, cloud, b->row_ptr, b->cols, b->knn_idx, b->knn_d2, b->row_lo, b->row_hi, row_ptr,
+                            cols, nnz, knn_idx, knn_d2, b->clouds_[cloud]);
 }
 
 sfc_status batch_free(sfc_batch b, void* cuda_stream) {
     if (!b) return SFC_ERR_INVALID;
     sfc::free_batch(b, static_cast<cudaStream_t>(cuda_stream));
     delete b;
+    return SFC_OK;
+}
+
+sfc_status batch_plan_create(const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                             const sfc_build_opts* opts, int64_t nnz_capacity, void* cuda_stream,
+                             sfc_batch_plan* out) {
+    if (!out) return SFC_ERR_INVALID;
+    *out = nullptr;
+    if (nnz_capacity < 0) return SFC_ERR_INVALID;
+    sfc_build_opts o;
+    int64_t total = 0;
+    SFC_TRY(sfc::check_batch_args(clouds, n_clouds, enc, opts, &o, &total));
+    if (total == 0) return SFC_ERR_INVALID;
+    int dev = 0;
+    SFC_CUDA(cudaGetDevice(&dev));
+    SFC_TRY(sfc::ensure_pool(dev));
+    cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
+    SFC_CUDA(cudaStreamSynchronize(user));  // the plan's buffers come from its own stream
+    sfc_batch_plan_s* P = new (std::nothrow) sfc_batch_plan_s;
+    if (!P) return SFC_ERR_OOM;
+    P->clouds.assign(clouds, clouds + n_clouds);
+    P->enc = enc;
+    P->o = o;
+    sfc::make_tables(clouds, n_clouds, o.leaf_capacity, P->T);
+    P->row_lo.assign(n_clouds, 0);
+    P->row_hi.assign(n_clouds, 0);
+    sfc_status st = SFC_OK;
+    auto fail = [&](sfc_status e) {
+        sfc::destroy_plan(P);
+        return e;
+    };
+    if (cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&P->host), sizeof(sfc_batch_plan_s::Status)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&P->host_bounds), sizeof(int64_t) * P->T.where.size()) !=
+            cudaSuccess)
+        return fail(SFC_ERR_CUDA);
+    P->mem = new (std::nothrow) sfc::Scratch(P->cs);
+    if (!P->mem) return fail(SFC_ERR_OOM);
+    sfc::Scratch& m = *P->mem;
+    const int64_t n = P->T.n_total;
+    int64_t radius_points = 0;
+    for (int t = 0; t < 4; ++t)
+        for (int64_t j = 0; j < P->T.count[t]; ++j) radius_points += P->T.table[P->T.off[t] + j].nq;
+    P->cols_cap = nnz_capacity > 0 ? nnz_capacity : 64 * radius_points;
+    if ((st = m.alloc(&P->xyz, 3 * n)) != SFC_OK || (st = sfc::alloc_base(P->T, P->b, m)) != SFC_OK ||
+        (st = m.alloc(&P->row_ptr, n + 1)) != SFC_OK || (st = m.alloc(&P->knn_idx, P->T.knn_total)) != SFC_OK ||
+        (st = m.alloc(&P->knn_d2, P->T.knn_total)) != SFC_OK ||
+        (st = sfc::dev_alloc(&P->cols, P->cols_cap, P->cs)) != SFC_OK ||
+        (st = sfc::plan_alloc_trees(P, P->T.int_bound)) != SFC_OK)
+        return fail(st);
+    sfc::alloc_records(P->T, P->b, m);
+    if ((st = sfc::upload_tables(P->T, P->b, P->cs)) != SFC_OK) return fail(st);
+    if (cudaMemsetAsync(P->xyz, 0, sizeof(float) * 3 * (n ? n : 1), P->cs) != cudaSuccess) return fail(SFC_ERR_CUDA);
+    if ((st = sfc::capture_plan(P)) != SFC_OK) return fail(st);
+    if (cudaStreamSynchronize(P->cs) != cudaSuccess) return fail(SFC_ERR_CUDA);
+    *out = P;
+    return SFC_OK;
+}
+
+sfc_status batch_plan_points(sfc_batch_plan p, float** points_xyz) {
+    if (!p || !points_xyz) return SFC_ERR_INVALID;
+    *points_xyz = p->xyz;
+    return SFC_OK;
+}
+
+sfc_status batch_plan_launch(sfc_batch_plan p, void* cuda_stream) {
+    if (!p) return SFC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!p->exec) SFC_TRY(sfc::capture_plan(p));
+    SFC_CUDA(cudaGraphLaunch(p->exec, s));
+    SFC_CUDA(cudaEventRecord(p->done, s));
+    sfc::count_launches(p->kernels_per_run);
+    p->launched = true;
+    p->ready = false;
+    return SFC_OK;
+}
+
+sfc_status batch_plan_finish(sfc_batch_plan p, void* cuda_stream) {
+    if (!p || !p->launched) return SFC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    SFC_CUDA(cudaEventSynchronize(p->done));
+    p->launched = false;
+    sfc::BatchTotals tot = p->host->tot;
+    if (tot.flags & sfc::kNonFinite) return SFC_ERR_NOT_FINITE;
+    if (tot.flags & sfc::kOverNodes) {
+        // the trees did not fit (the bound holds, so only a smaller capacity can do this)
+        if (tot.n_nodes > 0x7fffffffLL) return SFC_ERR_TOO_LARGE;
+        SFC_TRY(sfc::plan_alloc_trees(p, tot.n_int));
+        SFC_CUDA(cudaStreamSynchronize(p->cs));
+        SFC_TRY(sfc::capture_plan(p));
+        SFC_TRY(batch_plan_launch(p, cuda_stream));
+        return batch_plan_finish(p, cuda_stream);
+    }
+    if (tot.flags & sfc::kOverCols) {
+        // the radius output did not fit: grow it and run the fill again (the counts, row
+        // pointers and records of this run are still in place); the graph is recorded
+        // again with the new array before the next launch
+        sfc::release_cols(p);
+        p->cols_cap = tot.nnz + tot.nnz / 8;
+        if (cudaGraphExecDestroy(p->exec) == cudaSuccess) p->exec = nullptr;
+        SFC_TRY(sfc::dev_alloc(&p->cols, p->cols_cap, p->cs));
+        SFC_CUDA(cudaStreamSynchronize(p->cs));
+        const unsigned int keep = tot.flags & ~sfc::kOverCols;
+        SFC_CUDA(cudaMemcpyAsync(&p->b.tot->flags, &keep, sizeof keep, cudaMemcpyHostToDevice, s));
+        SFC_TRY(sfc::enqueue_radius_fill(p->T, p->b, p->o.prune, p->row_ptr, p->cols, p->cols_cap, s));
+        SFC_CUDA(cudaMemcpyAsync(p->host_bounds, p->b.bounds, sizeof(int64_t) * p->T.where.size(),
+                                 cudaMemcpyDeviceToHost, s));
+        SFC_CUDA(cudaMemcpyAsync(&p->host->err, p->b.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        SFC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (p->host->err & sfc::kGuardTripped) return SFC_ERR_INTERNAL;
+    for (int i = 0; i < p->T.n_clouds; ++i) {
+        p->row_lo[i] = p->host_bounds[2 * i];
+        p->row_hi[i] = p->host_bounds[2 * i + 1];
+    }
+    p->ready = true;
+    return SFC_OK;
+}
+
+sfc_status batch_plan_result(sfc_batch_plan p, int32_t cloud, const int64_t** row_ptr, const int32_t** cols,
+                             int64_t* nnz, const int32_t** knn_idx, const float** knn_d2) {
+    if (!p || !p->ready || cloud < 0 || cloud >= p->T.n_clouds) return SFC_ERR_INVALID;
+    return sfc::cloud_views(p->T, cloud, p->row_ptr, p->cols, p->knn_idx, p->knn_d2, p->row_lo, p->row_hi, row_ptr,
+                            cols, nnz, knn_idx, knn_d2, p->clouds[cloud]);
+}
+
+sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream) {
+    if (!p) return SFC_ERR_INVALID;
+    SFC_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    sfc::destroy_plan(p);
     return SFC_OK;
 }
 

@@ -118,6 +118,8 @@ __device__ __forceinline__ int find_search_seg(const SearchSeg* segs, int n, int
 // ---------------------------------------------------------------------------------
 // runtime (sfc_runtime.cu)
 void record_cuda_error(cudaError_t e, const char* where);
+// kernels launched by replaying a recorded graph (added to the launch counter)
+void count_launches(uint64_t n);
 // Called around every kernel launch: counts launches, records profiling events.
 void launch_begin(const char* name, cudaStream_t s);
 sfc_status launch_end(const char* name, cudaStream_t s);
@@ -141,6 +143,19 @@ class Scratch {
         ptrs_.push_back(v);
         *p = static_cast<T*>(v);
         return SFC_OK;
+    }
+    // The same without reporting a failure (for optional buffers).
+    template <typename T>
+    bool try_alloc(T** p, size_t count) {
+        void* v = nullptr;
+        if (cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s_) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        ptrs_.push_back(v);
+        *p = static_cast<T*>(v);
+        return true;
     }
     // Hand an allocation over to the caller (it is no longer freed by the guard).
     void release(const void* p);

@@ -43,6 +43,10 @@ struct KnnArgs {
     const SearchSeg* segs;
     int nsegs;
     int64_t ngroups;
+    // batched search: the launch does nothing when (*skip & skip_mask) != 0 (a capacity
+    // overflow found on the device earlier in the same stream)
+    const unsigned int* skip;
+    unsigned int skip_mask;
 };
 
 __device__ __forceinline__ float box_lower_bound(const NodeBox& b, float cx, float cy, float cz) {
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     int k = a.k;
     if (a.segs) {
         if (group >= a.ngroups) return;
+        if (a.skip && (*a.skip & a.skip_mask)) return;
         const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
         first = sg.q0 + (group - sg.group0) * 32;
         q_lo = sg.q0;
@@ -523,7 +528,8 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
 // all kNN clouds of one list-size class of a batch, in one launch (sfc_batch.cu)
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
                             int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
-                            int32_t* out_idx, float* out_d2, unsigned int* err, cudaStream_t s) {
+                            int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
+                            unsigned int skip_mask, cudaStream_t s) {
     if (ngroups == 0) return SFC_OK;
     KnnArgs a;
     memset(&a, 0, sizeof a);
@@ -542,6 +548,8 @@ sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeB
     a.segs = segs;
     a.nsegs = nsegs;
     a.ngroups = ngroups;
+    a.skip = skip;
+    a.skip_mask = skip_mask;
     const unsigned int grid = grid_for(ngroups, kKnnWarps);
     switch (kmax) {
     case 8: SFC_LAUNCH("batch_knn", s, k_knn_group<8>, grid, kKnnWarps * 32, 0, a); break;
@@ -608,6 +616,8 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.segs = nullptr;
         a.nsegs = 0;
         a.ngroups = (rows + 31) / 32;
+        a.skip = nullptr;
+        a.skip_mask = 0;
         // curve neighbours per side for the seeding window: at least k / 2 so that the k
         // nearest along the curve fill the heap; the staged span 32 + 2 * window - 1 fits 96
         a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? std::max<int64_t>(16, (k + 1) / 2) : 0;

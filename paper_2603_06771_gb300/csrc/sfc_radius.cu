@@ -61,6 +61,10 @@ struct RadiusArgs {
     const SearchSeg* segs;
     int nsegs;
     int64_t ngroups;
+    // batched search: the launch does nothing when (*skip & skip_mask) != 0 (a capacity
+    // overflow found on the device earlier in the same stream)
+    const unsigned int* skip;
+    unsigned int skip_mask;
 };
 
 // A record header is (chunk start, chunk size <= 32) for a leaf chunk, or
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
     float r = a.r, r2 = a.r2;
     if (a.segs) {
         if (group >= a.ngroups) return;  // whole warp
+        if (a.skip && (*a.skip & a.skip_mask)) return;
         const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
         first = sg.q0 + (group - sg.group0) * 32;
         q_end = sg.q0 + sg.nq;
@@ -449,6 +454,8 @@ static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, flo
     a.segs = nullptr;
     a.nsegs = 0;
     a.ngroups = (rows + 31) / 32;
+    a.skip = nullptr;
+    a.skip_mask = 0;
     return a;
 }
 
@@ -588,7 +595,8 @@ static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, c
 sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
                                int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kern,
                                bool fill, uint32_t* counts, const int64_t* row_ptr, int32_t* cols, unsigned int* err,
-                               int prune, const BatchRecords& rec, cudaStream_t s) {
+                               int prune, const BatchRecords& rec, const unsigned int* skip, unsigned int skip_mask,
+                               cudaStream_t s) {
     if (ngroups == 0) return SFC_OK;
     RadiusArgs a;
     memset(&a, 0, sizeof a);
@@ -607,6 +615,8 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
     a.segs = segs;
     a.nsegs = nsegs;
     a.ngroups = ngroups;
+    a.skip = skip;
+    a.skip_mask = skip_mask;
     if (rec.masks) {  // the count pass records hit masks, the fill replays them
         a.rec_mode = fill ? 2 : 1;
         a.rec_cap = kRecordCap;

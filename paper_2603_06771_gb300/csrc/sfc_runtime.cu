@@ -33,9 +33,13 @@ struct ProfRecord {
 static std::vector<ProfRecord> g_prof;
 static thread_local cudaEvent_t t_pending_start = nullptr;
 
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void launch_begin(const char* name, cudaStream_t s) {
     (void)name;
-    if (g_prof_on.load(std::memory_order_relaxed)) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (g_prof_on.load(std::memory_order_relaxed) && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {  // launches recorded into a graph are not timed
         cudaEvent_t e;
         if (cudaEventCreate(&e) == cudaSuccess) {
             cudaEventRecord(e, s);

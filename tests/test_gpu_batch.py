@@ -192,3 +192,87 @@ def test_batch_errors():
     b = sfc.batch_search(x, ok, "morton")  # the context is still usable
     assert b.knn(0)[0].shape == (100, 4)
     b.free()
+
+
+# ----------------------------------------------------------------------------- batch plans
+def _same(a, b, specs):
+    for i, sp in enumerate(specs):
+        if sp["search"] == "radius":
+            ra, rb = gpu_csr(*a.radius(i)), gpu_csr(*b.radius(i))
+            assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]), i
+        else:
+            ka, kb = a.knn(i), b.knn(i)
+            assert torch.equal(ka[0], kb[0]), i
+            assert torch.equal(ka[1].view(torch.int32), kb[1].view(torch.int32)), i
+
+
+@pytest.mark.parametrize("enc,ncap", [("hilbert", 32), ("morton", 8)])
+def test_plan_matches_batch_search(enc, ncap):
+    """A recorded plan gives batch_search's bytes (hence the oracle's), run after run."""
+    items = [it for it in MIX if it[0] != "empty"] + [MIX[2]]  # an empty cloud last
+    xyz = [cloud(name) for name, _ in items]
+    specs = [dict(spec, n=len(x)) for x, (_, spec) in zip(xyz, items)]
+    pts = dev(np.concatenate(xyz))
+    want = sfc.batch_search(pts, specs, enc, leaf_capacity=ncap)
+    plan = sfc.BatchPlan(specs, enc, leaf_capacity=ncap)
+    plan.points.copy_(pts)
+    before = sfc.launch_count()
+    plan.run()
+    per_run = sfc.launch_count() - before
+    assert per_run > 20
+    _same(plan, want, specs)
+    plan.run()  # a replay of the same graph
+    _same(plan, want, specs)
+    assert sfc.launch_count() - before == 2 * per_run
+    plan.free()
+    want.free()
+
+
+def test_plan_new_points_each_run():
+    xyz, specs = _random_batch(60, 17, 5000)
+    plan = sfc.BatchPlan(specs, "hilbert", leaf_capacity=16)
+    for seed in (0, 1):
+        pts = [x if seed == 0 else (x[::-1].copy() * np.float32(1.5)) for x in xyz]
+        p = dev(np.concatenate(pts))
+        plan.points.copy_(p)
+        plan.run()
+        _same(plan, sfc.batch_search(p, specs, "hilbert", leaf_capacity=16), specs)
+    plan.free()
+
+
+def test_plan_radius_output_overflow_regrows():
+    """A radius output capacity far too small: the run skips its fill, finish grows the
+    array to the exact size and fills again; the next run uses a graph recorded with it."""
+    items = [("uniform4097", dict(search="radius", kernel="sphere", r=0.1)),
+             ("clusters40k", dict(search="knn", k=16)),
+             ("lidar60k", dict(search="radius", kernel="cube", r=1.0))]
+    xyz = [cloud(name) for name, _ in items]
+    specs = [dict(spec, n=len(x)) for x, (_, spec) in zip(xyz, items)]
+    pts = dev(np.concatenate(xyz))
+    want = sfc.batch_search(pts, specs, "hilbert", leaf_capacity=32)
+    plan = sfc.BatchPlan(specs, "hilbert", leaf_capacity=32, nnz_capacity=1)
+    plan.points.copy_(pts)
+    plan.run()
+    _same(plan, want, specs)
+    plan.run()
+    _same(plan, want, specs)
+    plan.free()
+
+
+def test_plan_errors():
+    with pytest.raises(sfc.SFCError) as e:
+        sfc.BatchPlan([dict(n=0, search="knn", k=4)], "hilbert")
+    assert e.value.status == 1
+    plan = sfc.BatchPlan([dict(n=100, search="knn", k=4)], "hilbert")
+    with pytest.raises(sfc.SFCError):
+        plan.finish()  # nothing launched
+    bad = synth.uniform_cube(100, 3)
+    bad[5, 0] = np.nan
+    plan.points.copy_(dev(bad))
+    with pytest.raises(sfc.SFCError) as e:
+        plan.run()
+    assert e.value.status == 7
+    plan.points.copy_(dev(synth.uniform_cube(100, 3)))
+    plan.run()  # the plan is still usable
+    assert plan.knn(0)[0].shape == (100, 4)
+    plan.free()
