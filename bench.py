@@ -70,6 +70,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256"], default="lidar_tile_10M")
     ap.add_argument("--clouds", type=int, default=256, help="batch256: number of clouds (testing)")
+    ap.add_argument("--no-tune", action="store_true", help="batch256: one leaf capacity for every cloud")
     return ap.parse_args(argv)
 
 
@@ -294,9 +295,10 @@ def batch_setup(sfc, torch, n_clouds: int, ncap: int, enc: str):
 
 
 def plain_step(sfc, specs, views, enc: str, ncap: int):
-    """Every cloud through the single-cloud entry points, one after the other."""
+    """Every cloud through the single-cloud entry points, one after the other (each at the
+    leaf capacity the batch gives it)."""
     for sp, v in zip(specs, views):
-        t = sfc.octree_build(v, enc, leaf_capacity=ncap)
+        t = sfc.octree_build(v, enc, leaf_capacity=sp.get("leaf_capacity") or ncap)
         if sp["search"] == "radius":
             sfc.radius_search(t, None, sp["r"], sp["kernel"])
         else:
@@ -321,6 +323,14 @@ def batch_main(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     clouds = [dict(n=sp["n"], search=sp["search"], kernel=sp.get("kernel", "sphere"), r=sp.get("r", 0.0),
                    k=sp.get("k", 0)) for sp in specs]
+    tune_s = None
+    if not args.no_tune:  # per-cloud leaf capacity and kNN seeding window from the device autotuner
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        clouds = sfc.batch_autotune(pts, clouds, enc, leaf_capacity=ncap)
+        tune_s = time.perf_counter() - t0
+        for sp, c in zip(specs, clouds):
+            sp["leaf_capacity"], sp["knn_window"] = c["leaf_capacity"], c["knn_window"]
 
     def timed(fn, steps, warmup):
         for w in range(warmup):
@@ -386,6 +396,10 @@ def batch_main(args):
             "config": {"workload": "batch256", "clouds": len(specs), "points": n_total, "encoding": enc,
                        "leaf_capacity": ncap, "radius_clouds": n_radius, "knn_clouds": len(specs) - n_radius,
                        "radius_redrawn": redrawn, "nnz_cap_per_cloud": BATCH_NNZ_CAP,
+                       "autotune_s": tune_s,
+                       "leaf_capacity_chosen": sorted({int(c.get("leaf_capacity") or ncap) for c in clouds}),
+                       "knn_window_chosen": sorted({int(c.get("knn_window", 0)) for c in clouds
+                                                    if c["search"] == "knn"}),
                        "nnz": int(sum(sp.get("nnz", 0) for sp in specs)),
                        "l2": "flushed before every timed step (512 MiB write)"},
             "plain": {"value": units / (p_total / 1e3), "ms_per_step": p_total / args.steps},

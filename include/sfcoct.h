@@ -183,6 +183,9 @@ typedef struct {
     int32_t kernel;   /* SFC_SEARCH_RADIUS: sfc_kernel */
     float r;          /* SFC_SEARCH_RADIUS: radius (r <= 0 gives empty rows) */
     int32_t k;        /* SFC_SEARCH_KNN: neighbours, 1 <= k <= 64 */
+    int32_t leaf_capacity; /* this cloud's leaf capacity; 0 = opts->leaf_capacity */
+    int32_t knn_window;    /* SFC_SEARCH_KNN: curve neighbours per side that seed each list,
+                              0..32 (0 = max(16, (k + 1) / 2)); a speed knob only */
 } sfc_batch_cloud;
 
 typedef struct sfc_batch_s* sfc_batch; /* results of a batch, owned by the library */
@@ -218,6 +221,21 @@ sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_pt
 
 /* Release a batch's results (stream ordered on cuda_stream). */
 sfc_status batch_free(sfc_batch b, void* cuda_stream);
+
+/* Choose every cloud's leaf capacity and (kNN) seeding window for this batch by timing it:
+ * one pass per candidate leaf capacity (after one untimed warm pass), the build timed whole
+ * and every launch set (radius kernel type: count + fill; kNN list size 8/16/32/64) on its
+ * own with CUDA events; each set takes the capacity minimising its search time plus its
+ * points' share of the build time.  Then one pass per candidate window at those
+ * capacities picks each kNN set's window.  Writes leaf_capacity_out[n_clouds] and
+ * knn_window_out[n_clouds] (0 for radius clouds), ready for sfc_batch_cloud.  Results of a
+ * batch do not depend on either knob.  The paper has no counterpart (it fixes N_max per
+ * run).  Errors as batch_search, plus SFC_ERR_INVALID for a candidate < 1 or a window
+ * above 32.  Synchronises cuda_stream repeatedly. */
+sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                          const sfc_build_opts* opts, const int32_t* leaf_candidates, int32_t n_leaf,
+                          const int32_t* window_candidates, int32_t n_window, void* cuda_stream,
+                          int32_t* leaf_capacity_out, int32_t* knn_window_out);
 
 /* ---- batch plans: the batched pass recorded once as a CUDA graph and replayed --------- */
 

@@ -16,7 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
-    "Batch", "batch_search", "BatchPlan",
+    "Batch", "batch_search", "BatchPlan", "batch_autotune",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
 
@@ -77,6 +77,8 @@ _SIGNATURES = {
     "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
     "batch_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_int32,
+                                 C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "batch_plan_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "batch_plan_points": (C.c_int, [C.c_void_p, C.c_void_p]),
     "batch_plan_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -329,7 +331,7 @@ def profile_read() -> dict:
 # ----------------------------------------------------------------------------- batched path
 class _BatchCloud(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("search", C.c_int32), ("kernel", C.c_int32), ("r", C.c_float),
-                ("k", C.c_int32)]
+                ("k", C.c_int32), ("leaf_capacity", C.c_int32), ("knn_window", C.c_int32)]
 
 
 def _cloud_array(clouds: list):
@@ -337,7 +339,8 @@ def _cloud_array(clouds: list):
     for i, c in enumerate(clouds):
         radius = c.get("search", "radius") == "radius"
         arr[i] = _BatchCloud(int(c["n"]), 0 if radius else 1, _kern(c.get("kernel", "sphere")) if radius else 0,
-                             float(c.get("r", 0.0)), int(c.get("k", 0)))
+                             float(c.get("r", 0.0)), int(c.get("k", 0)), int(c.get("leaf_capacity", 0)),
+                             int(c.get("knn_window", 0)))
     return arr
 
 
@@ -457,3 +460,23 @@ class BatchPlan(Batch):
                 self._h = None
         except Exception:
             pass
+
+
+def batch_autotune(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_capacity: int = 32,
+                   prune: bool = True, leaf_candidates=(16, 32, 64, 128, 256), window_candidates=(16, 24, 32),
+                   stream=None) -> list:
+    """``batch_autotune`` of the C ABI: the clouds with ``leaf_capacity`` and (kNN)
+    ``knn_window`` filled in from timing this batch on the device."""
+    pts = _xyz(points, "points")
+    if sum(int(c["n"]) for c in clouds) != pts.shape[0]:
+        raise ValueError("the clouds' sizes must add up to the number of points")
+    arr = _cloud_array(clouds)
+    opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
+    lc = (C.c_int32 * len(leaf_candidates))(*leaf_candidates)
+    wc = (C.c_int32 * len(window_candidates))(*window_candidates)
+    leaf_out = (C.c_int32 * len(clouds))()
+    win_out = (C.c_int32 * len(clouds))()
+    _check(lib().batch_autotune(_ptr(pts), C.byref(arr), len(clouds), _enc(encoding), C.byref(opts), lc,
+                                len(leaf_candidates), wc, len(window_candidates), C.c_void_p(_stream(stream)),
+                                leaf_out, win_out), "batch_autotune")
+    return [dict(c, leaf_capacity=int(leaf_out[i]), knn_window=int(win_out[i])) for i, c in enumerate(clouds)]

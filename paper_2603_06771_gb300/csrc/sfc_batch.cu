@@ -462,7 +462,6 @@ struct BatchTables {
     std::vector<SearchSeg> table;      // launch tables, one slice per launch (roots set on the device)
     std::vector<int32_t> table_cloud;  // the cloud of every table entry
     int64_t off[kLaunchSets], count[kLaunchSets], groups[kLaunchSets];
-    int window[kLaunchSets];
     std::vector<int64_t> where;  // the row_ptr positions bounding every cloud's rows
     std::vector<int64_t> out0;   // kNN clouds: first output entry
     int64_t knn_total = 0;
@@ -483,8 +482,8 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
         memset(&g, 0, sizeof g);
         g.p0 = p;
         g.n = c.n_points;
-        g.ncap = ncap;
-        T.int_bound += internal_bound(c.n_points, ncap);
+        g.ncap = c.leaf_capacity > 0 ? c.leaf_capacity : ncap;
+        T.int_bound += internal_bound(c.n_points, g.ncap);
         T.where.push_back(p);
         T.where.push_back(p + c.n_points);
         if (c.n_points > 0) {
@@ -495,6 +494,7 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
             q.k = c.k;
             q.r = c.r;
             q.r2 = c.r * c.r;
+            q.window = c.knn_window > 0 ? c.knn_window : std::max(16, (c.k + 1) / 2);
             if (c.search == SFC_SEARCH_RADIUS) {
                 if (c.r > 0.f) {  // r <= 0: every row empty
                     q.row0 = p;
@@ -517,16 +517,13 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
         T.off[t] = static_cast<int64_t>(T.table.size());
         T.count[t] = static_cast<int64_t>(sets[t].size());
         int64_t g = 0;
-        int w = 16;  // curve neighbours per side for the kNN seeding window (at least k / 2)
         for (size_t j = 0; j < sets[t].size(); ++j) {
             sets[t][j].group0 = g;
             g += (sets[t][j].nq + 31) / 32;
-            w = std::max(w, (sets[t][j].k + 1) / 2);
             T.table.push_back(sets[t][j]);
             T.table_cloud.push_back(set_cloud[t][j]);
         }
         T.groups[t] = g;
-        T.window[t] = w;
         if (t < 4) T.rec_groups += g;
     }
 }
@@ -677,7 +674,7 @@ static sfc_status enqueue_knn(const BatchTables& T, BatchBuffers& b, int32_t* kn
     const int kmax_of[4] = {8, 16, 32, 64};
     for (int t = 4; t < kLaunchSets; ++t)
         SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
-                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.window[t], knn_idx, knn_d2,
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], 0, knn_idx, knn_d2,
                                  b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
     return SFC_OK;
 }
@@ -719,7 +716,7 @@ static sfc_status check_batch_args(const sfc_batch_cloud* clouds, int32_t n_clou
     *total = 0;
     for (int i = 0; i < n_clouds; ++i) {
         const sfc_batch_cloud& c = clouds[i];
-        if (c.n_points < 0) return SFC_ERR_INVALID;
+        if (c.n_points < 0 || c.leaf_capacity < 0 || c.knn_window < 0 || c.knn_window > 32) return SFC_ERR_INVALID;
         if (c.search == SFC_SEARCH_RADIUS) {
             if (c.kernel < 0 || c.kernel > 3 || isnan(c.r)) return SFC_ERR_INVALID;
         } else if (c.search == SFC_SEARCH_KNN) {
@@ -819,6 +816,117 @@ static sfc_status cloud_views(const BatchTables& T, int32_t cloud, const int64_t
     if (ki) *ki = radius ? nullptr : knn_idx + T.out0[cloud];
     if (kd) *kd = radius ? nullptr : knn_d2 + T.out0[cloud];
     return SFC_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// autotuning: one timed pass of the batch, the build timed whole and every launch set
+// (radius kernel type: count + fill; kNN list size) on its own, with CUDA events
+class EventTimer {
+  public:
+    explicit EventTimer(cudaStream_t s) : s_(s) {}
+    ~EventTimer() {
+        for (auto& e : ev_) cudaEventDestroy(e);
+    }
+    sfc_status mark(int* id) {
+        cudaEvent_t e;
+        SFC_CUDA(cudaEventCreate(&e));
+        ev_.push_back(e);
+        SFC_CUDA(cudaEventRecord(e, s_));
+        *id = static_cast<int>(ev_.size()) - 1;
+        return SFC_OK;
+    }
+    float ms(int a, int b) const {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev_[a], ev_[b]);
+        return t;
+    }
+
+  private:
+    cudaStream_t s_;
+    std::vector<cudaEvent_t> ev_;
+};
+
+static sfc_status timed_pass(const std::vector<sfc_batch_cloud>& clouds, const float* xyz, int enc,
+                             const sfc_build_opts& o, cudaStream_t s, float* build_ms, float* set_ms) {
+    BatchTables T;
+    make_tables(clouds.data(), static_cast<int>(clouds.size()), o.leaf_capacity, T);
+    const int64_t n = T.n_total;
+    Scratch tmp(s);
+    EventTimer ev(s);
+    BatchBuffers b;
+    b.int_cap = b.node_cap = b.leaf_cap = INT64_MAX;
+    SFC_TRY(alloc_base(T, b, tmp));
+    SFC_TRY(upload_tables(T, b, s));
+    int e0, ea, e1, e2;
+    SFC_TRY(ev.mark(&e0));
+    SFC_TRY(enqueue_order(T, b, xyz, enc, s, tmp));
+    SFC_TRY(ev.mark(&ea));
+    BatchTotals ht;
+    SFC_CUDA(cudaMemcpyAsync(&ht, b.tot, sizeof ht, cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    if (ht.flags & kNonFinite) return SFC_ERR_NOT_FINITE;
+    if (ht.flags & kOverNodes) return SFC_ERR_TOO_LARGE;
+    b.int_cap = ht.n_int;
+    b.node_cap = ht.n_nodes;
+    b.leaf_cap = ht.n_leaves;
+    SFC_TRY(alloc_trees(b, tmp));
+    SFC_TRY(ev.mark(&e1));
+    SFC_TRY(enqueue_trees(T, b, s));
+    SFC_TRY(ev.mark(&e2));
+    int32_t* knn_idx = nullptr;
+    float* knn_d2 = nullptr;
+    SFC_TRY(tmp.alloc(&knn_idx, T.knn_total));
+    SFC_TRY(tmp.alloc(&knn_d2, T.knn_total));
+    const int kmax_of[4] = {8, 16, 32, 64};
+    int mk[kLaunchSets][2];
+    for (int t = 4; t < kLaunchSets; ++t) {
+        SFC_TRY(ev.mark(&mk[t][0]));
+        SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], 0, knn_idx, knn_d2, b.err,
+                                 &b.tot->flags, kOverNodes | kNonFinite, s));
+        SFC_TRY(ev.mark(&mk[t][1]));
+    }
+    int64_t* row_ptr = nullptr;
+    SFC_TRY(tmp.alloc(&row_ptr, n + 1));
+    alloc_records(T, b, tmp);
+    SFC_CUDA(cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * n, s));
+    int mc[4][2], mf[4][2];
+    for (int kern = 0; kern < 4; ++kern) {
+        SFC_TRY(ev.mark(&mc[kern][0]));
+        SFC_TRY(batch_radius_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[kern],
+                                    static_cast<int>(T.count[kern]), T.groups[kern], kern, false, b.counts, nullptr,
+                                    nullptr, b.err, o.prune, records_of(T, b, kern), &b.tot->flags,
+                                    kOverNodes | kNonFinite, s));
+        SFC_TRY(ev.mark(&mc[kern][1]));
+    }
+    SFC_TRY(scan_u32_to_i64(b.counts, row_ptr, n, s, tmp));
+    int64_t nnz = 0;
+    SFC_CUDA(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof nnz, cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    int32_t* cols = nullptr;
+    SFC_TRY(tmp.alloc(&cols, nnz));
+    for (int kern = 0; kern < 4; ++kern) {
+        SFC_TRY(ev.mark(&mf[kern][0]));
+        SFC_TRY(batch_radius_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[kern],
+                                    static_cast<int>(T.count[kern]), T.groups[kern], kern, true, b.counts, row_ptr,
+                                    cols, b.err, o.prune, records_of(T, b, kern), &b.tot->flags,
+                                    kOverNodes | kNonFinite, s));
+        SFC_TRY(ev.mark(&mf[kern][1]));
+    }
+    unsigned int herr = 0;
+    SFC_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof herr, cudaMemcpyDeviceToHost, s));
+    SFC_CUDA(cudaStreamSynchronize(s));
+    if (herr & kGuardTripped) return SFC_ERR_INTERNAL;
+    *build_ms = ev.ms(e0, ea) + ev.ms(e1, e2);  // the host wait between the two is not build time
+    for (int kern = 0; kern < 4; ++kern) set_ms[kern] = ev.ms(mc[kern][0], mc[kern][1]) + ev.ms(mf[kern][0], mf[kern][1]);
+    for (int t = 4; t < kLaunchSets; ++t) set_ms[t] = ev.ms(mk[t][0], mk[t][1]);
+    return SFC_OK;
+}
+
+static int launch_set_of(const sfc_batch_cloud& c) {
+    if (c.n_points == 0) return -1;
+    if (c.search == SFC_SEARCH_RADIUS) return c.r > 0.f ? c.kernel : -1;
+    return 4 + (c.k <= 8 ? 0 : (c.k <= 16 ? 1 : (c.k <= 32 ? 2 : 3)));
 }
 
 }  // namespace sfc
@@ -1112,6 +1220,87 @@ sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream) {
     if (!p) return SFC_ERR_INVALID;
     SFC_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
     sfc::destroy_plan(p);
+    return SFC_OK;
+}
+
+
+sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
+                          const sfc_build_opts* opts, const int32_t* leaf_candidates, int32_t n_leaf,
+                          const int32_t* window_candidates, int32_t n_window, void* cuda_stream,
+                          int32_t* leaf_capacity_out, int32_t* knn_window_out) {
+    sfc_build_opts o;
+    int64_t total = 0;
+    SFC_TRY(sfc::check_batch_args(clouds, n_clouds, enc, opts, &o, &total));
+    if (!leaf_capacity_out || !knn_window_out || n_leaf < 0 || n_window < 0 || (n_leaf > 0 && !leaf_candidates) ||
+        (n_window > 0 && !window_candidates))
+        return SFC_ERR_INVALID;
+    for (int i = 0; i < n_leaf; ++i)
+        if (leaf_candidates[i] < 1) return SFC_ERR_INVALID;
+    for (int i = 0; i < n_window; ++i)
+        if (window_candidates[i] < 1 || window_candidates[i] > 32) return SFC_ERR_INVALID;
+    if (total > 0 && (!points_xyz || !sfc::is_device_ptr(points_xyz))) return SFC_ERR_NOT_DEVICE_PTR;
+    int dev = 0;
+    SFC_CUDA(cudaGetDevice(&dev));
+    SFC_TRY(sfc::ensure_pool(dev));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    constexpr int kSets = sfc::kLaunchSets;
+    std::vector<sfc_batch_cloud> cl(clouds, clouds + n_clouds);
+    std::vector<int64_t> set_points(kSets, 0);
+    for (const auto& c : cl) {
+        const int t = sfc::launch_set_of(c);
+        if (t >= 0) set_points[t] += c.n_points;
+    }
+    // leaf capacity per launch set: its searches plus its share of the build
+    int32_t best_leaf[kSets];
+    float best_cost[kSets];
+    for (int t = 0; t < kSets; ++t) {
+        best_leaf[t] = o.leaf_capacity;
+        best_cost[t] = INFINITY;
+    }
+    if (total > 0) {
+        for (int i = 0; i < n_leaf; ++i) {
+            for (auto& c : cl) {
+                c.leaf_capacity = leaf_candidates[i];
+                c.knn_window = 0;
+            }
+            float build = 0.f, set_ms[kSets];
+            SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));  // warm
+            SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));
+            for (int t = 0; t < kSets; ++t) {
+                if (set_points[t] == 0) continue;
+                const float cost = set_ms[t] + build * static_cast<float>(set_points[t]) / static_cast<float>(total);
+                if (cost < best_cost[t]) {
+                    best_cost[t] = cost;
+                    best_leaf[t] = leaf_candidates[i];
+                }
+            }
+        }
+    }
+    // seeding window per kNN launch set, at the chosen leaf capacities
+    int32_t best_window[kSets] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float best_knn[kSets];
+    for (int t = 0; t < kSets; ++t) best_knn[t] = INFINITY;
+    for (int i = 0; i < n_window && total > 0; ++i) {
+        for (auto& c : cl) {
+            const int t = sfc::launch_set_of(c);
+            c.leaf_capacity = t >= 0 ? best_leaf[t] : 0;
+            c.knn_window = window_candidates[i];
+        }
+        float build = 0.f, set_ms[kSets];
+        SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));
+        for (int t = 4; t < kSets; ++t) {
+            if (set_points[t] == 0) continue;
+            if (set_ms[t] < best_knn[t]) {
+                best_knn[t] = set_ms[t];
+                best_window[t] = window_candidates[i];
+            }
+        }
+    }
+    for (int i = 0; i < n_clouds; ++i) {
+        const int t = sfc::launch_set_of(clouds[i]);
+        leaf_capacity_out[i] = t >= 0 ? best_leaf[t] : o.leaf_capacity;
+        knn_window_out[i] = t >= 4 ? best_window[t] : 0;
+    }
     return SFC_OK;
 }
 

@@ -102,6 +102,8 @@ struct SearchSeg {
     int32_t root;    // its root node
     int32_t k;       // kNN: neighbours
     float r, r2;     // radius and fl(r * r)
+    int32_t window;  // kNN: curve neighbours per side for the seeding window (0: none)
+    int32_t pad;
 };
 
 // Index of the cloud that owns warp group `group` (the last entry with group0 <= group).

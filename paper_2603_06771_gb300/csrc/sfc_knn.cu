@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     int64_t first = group * 32, q_lo = 0, q_end = a.nq, out0 = 0;
     int32_t root = 0;
     int k = a.k;
+    int64_t window = a.window;
     if (a.segs) {
         if (group >= a.ngroups) return;
         if (a.skip && (*a.skip & a.skip_mask)) return;
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
         out0 = sg.row0;
         root = sg.root;
         k = sg.k;
+        window = sg.window;
     } else if (first >= a.nq) {
         return;
     }
@@ -306,26 +308,26 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     // skips those positions.
     int64_t win_lo = 0;
     uint32_t win_n = 0;
-    if (a.window > 0 && 32 + 2 * a.window - 1 <= kBuf) {
-        const int64_t r0 = first - (a.window - 1);  // staged positions r0 .. r0 + 95
+    if (window > 0 && 32 + 2 * window - 1 <= kBuf) {
+        const int64_t r0 = first - (window - 1);  // staged positions r0 .. r0 + 95
         for (int j = lane; j < kBuf; j += 32) {
             const int64_t pos = r0 + j;
             buf[j] = (pos >= q_lo && pos < q_end) ? __ldg(&a.pts[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
         const int64_t p = qi;
-        win_lo = p - a.window + 1;
-        win_n = static_cast<uint32_t>(2 * a.window);
+        win_lo = p - window + 1;
+        win_n = static_cast<uint32_t>(2 * window);
         auto window_key = [&](int t) -> uint64_t {
             const int64_t pos = p + ((t & 1) ? (t + 1) / 2 : -(t / 2));
             if (!active || pos < q_lo || pos >= q_end) return kNoPair;
             return key_of(buf[pos - r0]);
         };
-        const int nfill = min(k, static_cast<int>(2 * a.window));
+        const int nfill = min(k, static_cast<int>(2 * window));
         for (int t = 0; t < k; ++t) best.at(t) = t < nfill ? window_key(t) : kNoPair;
         best.heapify();
-        for (int t0 = nfill; t0 < 2 * a.window; t0 += 32) {
-            const int span = min(32, 2 * static_cast<int>(a.window) - t0);
+        for (int t0 = nfill; t0 < 2 * window; t0 += 32) {
+            const int span = min(32, 2 * static_cast<int>(window) - t0);
             uint32_t cand = 0;
             const float kd = best.kth_d2();
 #pragma unroll 8

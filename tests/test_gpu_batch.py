@@ -276,3 +276,35 @@ def test_plan_errors():
     plan.run()  # the plan is still usable
     assert plan.knn(0)[0].shape == (100, 4)
     plan.free()
+
+
+# ----------------------------------------------------------------------------- per-cloud knobs and the tuner
+def test_per_cloud_leaf_capacity_and_window_keep_results():
+    """Leaf capacity and seeding window are speed knobs: any per-cloud choice gives the
+    same bytes (each cloud equals its single-cloud run at its own capacity)."""
+    xyz, specs = _random_batch(24, 19, 5000)
+    caps = [16, 64, 256, 8, 33, 1]
+    wins = [1, 8, 16, 32, 0, 5]
+    for i, sp in enumerate(specs):
+        sp["leaf_capacity"] = caps[i % len(caps)]
+        if sp["search"] == "knn":
+            sp["knn_window"] = wins[i % len(wins)]
+    b = sfc.batch_search(dev(np.concatenate(xyz)), specs, "hilbert", leaf_capacity=32)
+    for i, (x, sp) in enumerate(zip(xyz, specs)):
+        want = _single(x, sp, "hilbert", sp["leaf_capacity"])
+        got = gpu_csr(*b.radius(i)) if sp["search"] == "radius" else tuple(v.cpu().numpy() for v in b.knn(i))
+        assert np.array_equal(got[0], want[0]), i
+        assert np.array_equal(got[1].view(np.uint32), want[1].view(np.uint32)), i
+    b.free()
+
+
+def test_autotune_choices_are_valid_and_keep_results():
+    xyz, specs = _random_batch(30, 23, 8000)
+    pts = dev(np.concatenate(xyz))
+    tuned = sfc.batch_autotune(pts, specs, "hilbert", leaf_candidates=(16, 64), window_candidates=(16, 32))
+    for sp, t in zip(specs, tuned):
+        assert t["leaf_capacity"] in (16, 32, 64)  # 32: clouds without a search keep the default
+        assert t["knn_window"] in ((16, 32) if sp["search"] == "knn" and sp["n"] > 0 else (0,))
+    _same(sfc.batch_search(pts, tuned, "hilbert"), sfc.batch_search(pts, specs, "hilbert"), specs)
+    with pytest.raises(sfc.SFCError):
+        sfc.batch_autotune(pts, specs, "hilbert", window_candidates=(33,))
