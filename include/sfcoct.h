@@ -278,6 +278,83 @@ sfc_status batch_plan_result(sfc_batch_plan p, int32_t cloud, const int64_t** ro
 /* Release the plan (waits for cuda_stream first). */
 sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream);
 
+/* ---- serving: requests that arrive at any time ------------------------------------ */
+
+typedef struct sfc_server_s* sfc_server; /* owned by the library */
+
+typedef struct {
+    int32_t slots;         /* requests (or merged groups) on the device at once, 1..16; one
+                              worker thread and one CUDA stream each */
+    int32_t max_batch;     /* all-points requests merged into one batched pass, 1..1024 */
+    int64_t batch_points;  /* merge all-points requests of at most this many points, and at
+                              most this many points per merged pass (0: never merge) */
+    int64_t hbm_budget;    /* bytes: a request is admitted while the admitted, unreleased ones
+                              plus its estimate stay within this (one larger than the whole
+                              budget runs alone) */
+    sfc_encoding enc;      /* SFC_ENC_MORTON or SFC_ENC_HILBERT */
+    int32_t leaf_capacity;
+} sfc_server_opts;
+
+typedef struct {
+    const float* points_xyz;  /* host, n_points x 3 float32; read until the request finishes */
+    int64_t n_points;
+    const float* queries_xyz; /* host, n_queries x 3, or NULL: every point is a centre */
+    int64_t n_queries;
+    int32_t search;           /* sfc_search_kind */
+    int32_t kernel;           /* radius: sfc_kernel */
+    float r;                  /* radius */
+    int32_t k;                /* kNN: 1..64 */
+} sfc_request;
+
+typedef struct {
+    const int64_t* row_ptr;   /* radius: device, n_rows + 1 entries; row i is
+                                 cols[row_ptr[i] - row_base .. row_ptr[i + 1] - row_base) */
+    const int32_t* cols;      /* radius: device, nnz entries (ids are positions in the cloud) */
+    int64_t nnz;
+    int64_t row_base;
+    const int32_t* knn_idx;   /* kNN: device, n_rows x k (layout of knn()) */
+    const float* knn_d2;
+    int64_t n_rows;
+    double latency_ms;        /* submit to result resident on the device */
+    double queue_ms;          /* submit to admission */
+    int32_t batched_with;     /* requests in its device pass (1: alone) */
+    int32_t pad;
+} sfc_request_result;
+
+typedef struct {
+    int64_t queued, running, admitted, reserved_bytes;
+} sfc_server_stats;
+
+/* Defaults: 4 slots, merge up to 64 all-points requests of <= 4M points in all, 150 GiB,
+ * Hilbert, leaf capacity 64. */
+sfc_status sfc_server_opts_default(sfc_server_opts* o);
+
+/* Start a server on the current device (worker threads and streams).  The requests' work
+ * is the plain method's (octree_build + radius_search / knn, or batch_search for merged
+ * all-points requests): a result does not depend on the requests that ran beside it.
+ * The paper serves one query set at a time; this is the serving layer around it. */
+sfc_status server_create(const sfc_server_opts* opts, sfc_server* out);
+
+/* Queue a request (non-blocking; its arrival time is now).  SFC_ERR_INVALID /
+ * SFC_ERR_TOO_LARGE for bad arguments; failures of the work itself are reported by
+ * server_wait. */
+sfc_status server_submit(sfc_server s, const sfc_request* req, int64_t* id);
+
+/* Wait for a request (timeout_ms < 0: no limit): SFC_ERR_TIMEOUT if it has not finished
+ * in time, else SFC_OK with *result = the request's own status. */
+sfc_status server_wait(sfc_server s, int64_t id, int32_t timeout_ms, sfc_status* result);
+
+/* Device views and timings of a finished request; valid until server_release. */
+sfc_status server_result(sfc_server s, int64_t id, sfc_request_result* out);
+
+/* Free a finished request's octree and results (its memory leaves the budget). */
+sfc_status server_release(sfc_server s, int64_t id);
+
+sfc_status server_stats(sfc_server s, sfc_server_stats* out);
+
+/* Finish the queued requests, stop the workers and free everything. */
+sfc_status server_destroy(sfc_server s);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------ */
 
 /* Copy the sorted codes (n), the permutation sorted position -> original index (n), the

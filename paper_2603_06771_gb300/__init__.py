@@ -3,13 +3,14 @@
 The compute path is the CUDA library ``libsfcoct.so`` (sources in ``csrc/``, C ABI in
 ``include/sfcoct.h``); this package builds it (:mod:`.build`) and binds it with ctypes
 (:mod:`.binding`).  See ``octree_build``, ``radius_search`` and ``knn``; many clouds at once
-with ``batch_search``, ``BatchPlan`` (a recorded CUDA graph) and ``batch_autotune``.
+with ``batch_search``, ``BatchPlan`` (a recorded CUDA graph) and ``batch_autotune``; requests
+arriving over time with ``Server``.
 """
-from .binding import (ENCODINGS, KERNELS, Batch, BatchPlan, Octree, SFCError, batch_autotune, batch_search,
-                      encode_cells, knn, launch_count, library_path, octree_build, profile_enable, profile_read,
-                      radius_count, radius_fill, radius_search, radius_search_csr)
+from .binding import (ENCODINGS, KERNELS, Batch, BatchPlan, Octree, Server, SFCError, batch_autotune,
+                      batch_search, encode_cells, knn, launch_count, library_path, octree_build, profile_enable,
+                      profile_read, radius_count, radius_fill, radius_search, radius_search_csr)
 from .build import build
 
-__all__ = ["ENCODINGS", "KERNELS", "Batch", "BatchPlan", "Octree", "SFCError", "batch_autotune", "batch_search",
-           "build", "encode_cells", "knn", "launch_count", "library_path", "octree_build", "profile_enable",
-           "profile_read", "radius_count", "radius_fill", "radius_search", "radius_search_csr"]
+__all__ = ["ENCODINGS", "KERNELS", "Batch", "BatchPlan", "Octree", "Server", "SFCError", "batch_autotune",
+           "batch_search", "build", "encode_cells", "knn", "launch_count", "library_path", "octree_build",
+           "profile_enable", "profile_read", "radius_count", "radius_fill", "radius_search", "radius_search_csr"]

@@ -16,7 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
-    "Batch", "batch_search", "BatchPlan", "batch_autotune",
+    "Batch", "batch_search", "BatchPlan", "batch_autotune", "Server",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
 
@@ -79,6 +79,14 @@ _SIGNATURES = {
     "batch_free": (C.c_int, [C.c_void_p, C.c_void_p]),
     "batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_int32,
                                  C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sfc_server_opts_default": (C.c_int, [C.c_void_p]),
+    "server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "server_result": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "server_release": (C.c_int, [C.c_void_p, C.c_int64]),
+    "server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "server_destroy": (C.c_int, [C.c_void_p]),
     "batch_plan_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "batch_plan_points": (C.c_int, [C.c_void_p, C.c_void_p]),
     "batch_plan_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -480,3 +488,126 @@ def batch_autotune(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_
                                 len(leaf_candidates), wc, len(window_candidates), C.c_void_p(_stream(stream)),
                                 leaf_out, win_out), "batch_autotune")
     return [dict(c, leaf_capacity=int(leaf_out[i]), knn_window=int(win_out[i])) for i, c in enumerate(clouds)]
+
+
+# ----------------------------------------------------------------------------- serving
+class _ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("batch_points", C.c_int64),
+                ("hbm_budget", C.c_int64), ("enc", C.c_int), ("leaf_capacity", C.c_int32)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("points_xyz", C.c_void_p), ("n_points", C.c_int64), ("queries_xyz", C.c_void_p),
+                ("n_queries", C.c_int64), ("search", C.c_int32), ("kernel", C.c_int32), ("r", C.c_float),
+                ("k", C.c_int32)]
+
+
+class _RequestResult(C.Structure):
+    _fields_ = [("row_ptr", C.c_void_p), ("cols", C.c_void_p), ("nnz", C.c_int64), ("row_base", C.c_int64),
+                ("knn_idx", C.c_void_p), ("knn_d2", C.c_void_p), ("n_rows", C.c_int64), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("batched_with", C.c_int32), ("pad", C.c_int32)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("admitted", C.c_int64),
+                ("reserved_bytes", C.c_int64)]
+
+
+def _host_xyz(a, what: str):
+    """A C-contiguous float32 (n, 3) host array (numpy or CPU tensor) the server may read."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise ValueError(f"{what} must be in host memory")
+        a = a.contiguous()
+        if a.dtype != torch.float32 or a.dim() != 2 or a.shape[1] != 3:
+            raise ValueError(f"{what} must be float32 of shape (n, 3)")
+        return a, a.data_ptr(), a.shape[0]
+    import numpy as np
+
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError(f"{what} must be of shape (n, 3)")
+    return a, a.ctypes.data, a.shape[0]
+
+
+class Server:
+    """``server_*`` of the C ABI: requests queued at any time, admitted against a device
+    memory budget, run on ``slots`` streams, small all-points requests merged."""
+
+    def __init__(self, slots: int = 4, max_batch: int = 64, batch_points: int = 4_000_000,
+                 hbm_budget: int = 150 << 30, encoding="hilbert", leaf_capacity: int = 64):
+        o = _ServerOpts(int(slots), int(max_batch), int(batch_points), int(hbm_budget), _enc(encoding),
+                        int(leaf_capacity))
+        h = C.c_void_p()
+        _check(lib().server_create(C.byref(o), C.byref(h)), "server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, points, search: str = "radius", kernel: str = "sphere", r: float = 0.0, k: int = 0,
+               queries=None) -> int:
+        pts, pptr, n = _host_xyz(points, "points")
+        q, qptr, nq = (None, None, 0) if queries is None else _host_xyz(queries, "queries")
+        radius = search == "radius"
+        req = _Request(pptr if n else None, n, qptr if q is not None else None, nq, 0 if radius else 1,
+                       _kern(kernel) if radius else 0, float(r), int(k))
+        rid = C.c_int64()
+        _check(lib().server_submit(self._h, C.byref(req), C.byref(rid)), "server_submit")
+        self._keep[rid.value] = (pts, q, search, int(k))
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> int:
+        st = C.c_int()
+        _check(lib().server_wait(self._h, int(rid), int(timeout_ms), C.byref(st)), "server_wait")
+        return st.value
+
+    def result(self, rid: int) -> dict:
+        """Copies of a finished request's results (torch, on the device) and its timings."""
+        res = _RequestResult()
+        _check(lib().server_result(self._h, int(rid), C.byref(res)), "server_result")
+        _, _, search, k = self._keep[rid]
+        out = {"latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "batched_with": res.batched_with,
+               "rows": res.n_rows}
+        n = res.n_rows
+        if search == "radius":
+            rp = torch.as_tensor(_DeviceArray(self, res.row_ptr, n + 1, "<i8"), device="cuda").clone()
+            out["row_ptr"] = rp - res.row_base
+            out["cols"] = (torch.as_tensor(_DeviceArray(self, res.cols, res.nnz, "<i4"), device="cuda").clone()
+                           if res.nnz else torch.empty(0, dtype=torch.int32, device="cuda"))
+        else:
+            if n:
+                out["knn_idx"] = torch.as_tensor(_DeviceArray(self, res.knn_idx, n * k, "<i4"),
+                                                 device="cuda").view(n, k).clone()
+                out["knn_d2"] = torch.as_tensor(_DeviceArray(self, res.knn_d2, n * k, "<f4"),
+                                                device="cuda").view(n, k).clone()
+            else:
+                out["knn_idx"] = torch.empty((0, k), dtype=torch.int32, device="cuda")
+                out["knn_d2"] = torch.empty((0, k), dtype=torch.float32, device="cuda")
+        return out
+
+    def timings(self, rid: int) -> dict:
+        res = _RequestResult()
+        _check(lib().server_result(self._h, int(rid), C.byref(res)), "server_result")
+        return {"latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "batched_with": res.batched_with,
+                "rows": res.n_rows}
+
+    def release(self, rid: int):
+        _check(lib().server_release(self._h, int(rid)), "server_release")
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().server_stats(self._h, C.byref(st)), "server_stats")
+        return {"queued": st.queued, "running": st.running, "admitted": st.admitted,
+                "reserved_bytes": st.reserved_bytes}
+
+    def close(self):
+        if self._h is not None:
+            _check(lib().server_destroy(self._h), "server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
