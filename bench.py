@@ -9,6 +9,8 @@ workload (weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+--workload serving replays a seeded Poisson trace of requests (200/s) through the request
+server and through a one-request-at-a-time server, reporting queries/s and p50/p99 latency.
 --workload batch256 times the batched path instead: 256 clouds of uneven sizes
 (log-uniform 10k-2M points, uniform / LiDAR / Gaussian clusters), each with an
 all-points sphere or kNN search, answered by one batch_search per step, next to the
@@ -68,7 +70,11 @@ def parse_args(argv=None):
     ap.add_argument("--k", type=int, default=WORKLOAD["knn_k"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256"], default="lidar_tile_10M")
+    ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving"], default="lidar_tile_10M")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--no-big", action="store_true", help="serving: leave out the 200M-point cloud")
     ap.add_argument("--clouds", type=int, default=256, help="batch256: number of clouds (testing)")
     ap.add_argument("--no-tune", action="store_true", help="batch256: one leaf capacity for every cloud")
     return ap.parse_args(argv)
@@ -415,11 +421,150 @@ def batch_main(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving workload
+SERVE_METRIC = "served queries/s on 1 GB300 with p50/p99 request latency (Poisson arrivals, LiDAR-like clouds)"
+
+
+def serve_trace(seconds: float, rate: float, pool_sizes: list, seed: int):
+    """Request arrivals (Poisson, seeded) with their cloud (a pool index, drawn by a
+    log-uniform size on [50k, 20M]), centres (all points or a seeded 1 % subset) and search
+    (half sphere r in {0.5, 1, 2, 3} m, half kNN k in {8, 16, 32})."""
+    import synth
+
+    rng = synth.Rng(seed)
+    n_max = int(seconds * rate * 2 + 16)
+    gaps = -np.log(1.0 - rng.u01(0, n_max)) / rate
+    t = np.cumsum(gaps)
+    t = t[t < seconds]
+    m = len(t)
+    size = np.exp(np.log(50_000) + rng.u01(1, m) * (np.log(20_000_000) - np.log(50_000)))
+    logs = np.log(np.asarray(pool_sizes, dtype=np.float64))
+    pick = np.abs(np.log(size)[:, None] - logs[None, :]).argmin(axis=1)
+    subset = rng.u01(2, m) < 0.5
+    radius = rng.u01(3, m) < 0.5
+    ri = rng.integers(4, m, 4)
+    ki = rng.integers(5, m, 3)
+    reqs = []
+    for i in range(m):
+        spec = (dict(search="radius", kernel="sphere", r=synth.BATCH_RADII[int(ri[i])]) if radius[i]
+                else dict(search="knn", k=synth.BATCH_KS[int(ki[i])]))
+        reqs.append(dict(t=float(t[i]), cloud=int(pick[i]), subset=bool(subset[i]), seed=seed * 7919 + i, **spec))
+    return reqs
+
+
+def serve_run(sfc, torch, trace, pool, big, server_kw):
+    """Replay the trace against one server: a submitting thread sleeps until each arrival,
+    the main thread waits for the requests in order and releases them."""
+    import threading
+
+    import synth
+
+    srv = sfc.Server(**server_kw)
+    ids = [None] * len(trace)
+    ready = [threading.Event() for _ in trace]
+    subsets = {}
+    for i, rq in enumerate(trace):  # the centres of subset requests, drawn before the clock starts
+        if rq["subset"]:
+            xyz = big if rq["cloud"] < 0 else pool[rq["cloud"]]
+            n = xyz.shape[0]
+            rows = np.sort(synth.Rng(rq["seed"]).integers(0, max(1, n // 100), n))
+            subsets[i] = torch.from_numpy(np.ascontiguousarray(xyz.numpy()[rows])).pin_memory()
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, rq in enumerate(trace):
+            delay = rq["t"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            xyz = big if rq["cloud"] < 0 else pool[rq["cloud"]]
+            kw = {k: rq[k] for k in ("search", "kernel", "r", "k") if k in rq}
+            ids[i] = srv.submit(xyz, queries=subsets.get(i), **kw)
+            ready[i].set()
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, queued, merged, queries = [], [], [], 0
+    for i in range(len(trace)):
+        ready[i].wait()
+        st = srv.wait(ids[i])
+        if st != 0:
+            raise RuntimeError(f"request {i} failed with status {st}")
+        tm = srv.timings(ids[i])
+        lat.append(tm["latency_ms"])
+        queued.append(tm["queue_ms"])
+        merged.append(tm["batched_with"])
+        queries += tm["rows"]
+        srv.release(ids[i])
+    makespan = time.perf_counter() - t0
+    th.join()
+    srv.close()
+    lat = np.asarray(lat)
+    return {"queries_per_s": queries / makespan, "requests": len(trace), "queries": queries,
+            "makespan_s": makespan, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "mean_queue_ms": float(np.mean(queued)),
+            "merged_requests": int(sum(1 for b in merged if b > 1))}
+
+
+def serve_main(args):
+    import torch
+
+    import paper_2603_06771_gb300 as sfc
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    sfc.build()
+    pool_sizes = [int(round(x)) for x in np.exp(np.linspace(np.log(50_000), np.log(20_000_000), 16))]
+    pool = [torch.from_numpy(synth.lidar_tile(n, synth.CONFIG_SEED[5] * 100 + j)).pin_memory()
+            for j, n in enumerate(pool_sizes)]
+    big = None
+    trace = serve_trace(args.serve_seconds, args.serve_rate, pool_sizes, synth.CONFIG_SEED[5] + rank)
+    if not args.no_big:  # one 200M-point cloud at 20 pts/m^2 (10 km^2), 1 % of its points as centres
+        big = torch.from_numpy(synth.lidar_tile(200_000_000, synth.CONFIG_SEED[5] * 100 + 99,
+                                                side=float(np.sqrt(200_000_000 / 20.0)))).pin_memory()
+        mid = next(i for i, rq in enumerate(trace) if rq["t"] >= args.serve_seconds / 2)
+        trace.insert(mid, dict(t=trace[mid]["t"], cloud=-1, subset=True, seed=12345, search="radius",
+                               kernel="sphere", r=2.0))
+    kw = dict(slots=args.serve_slots, max_batch=64, batch_points=4_000_000, hbm_budget=150 << 30,
+              encoding=args.encoding, leaf_capacity=args.leaf_capacity)
+    warm = serve_trace(1.0, 20.0, pool_sizes, 7)  # loads the library paths and the memory pool
+    serve_run(sfc, torch, warm, pool, big, kw)
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks.start()
+    launches0 = sfc.launch_count()
+    ours = serve_run(sfc, torch, trace, pool, big, kw)
+    launches = sfc.launch_count() - launches0
+    plain = serve_run(sfc, torch, trace, pool, big, dict(kw, slots=1, max_batch=1, batch_points=0))
+    clk = clocks.stop()
+    if rank == 0:
+        line = {
+            "metric": SERVE_METRIC, "value": ours["queries_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": ours["makespan_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving", "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                       "cloud_sizes": "log-uniform 50k-20M (16 LiDAR-like pool clouds, pinned host memory)",
+                       "big_cloud": None if args.no_big else "200M points, 20 pts/m^2, 1% centres, sphere r=2",
+                       "centres": "50% all points, 50% seeded 1% subset",
+                       "searches": "50% sphere r in {0.5,1,2,3} m, 50% kNN k in {8,16,32}",
+                       "hbm_budget_gib": 150, "slots": args.serve_slots, "encoding": args.encoding,
+                       "leaf_capacity": args.leaf_capacity,
+                       "latency": "submit to result resident on the device"},
+            "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"], "serving": ours,
+            "plain": plain, "speedup_vs_plain": ours["queries_per_s"] / plain["queries_per_s"],
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
     if args.workload == "batch256" and args.impl == "ours":
         return batch_main(args)
+    if args.workload == "serving" and args.impl == "ours":
+        return serve_main(args)
     cfg = dict(WORKLOAD, leaf_capacity=args.leaf_capacity, encoding=args.encoding, knn_k=args.k,
                radius={"kernel": args.kernel, "r": args.radius})
     if args.impl == "reference":
