@@ -159,6 +159,25 @@ int64_t radius_count_static_max_points(void);
 /* Free a CSR allocated by radius_search (stream ordered); zeroes *csr. */
 sfc_status sfc_csr_free(sfc_csr* csr, void* cuda_stream);
 
+/* Range output of a fixed-radius search (neighboursStruct, section 5.1): row i lists its
+ * neighbours as runs of consecutive positions of the octree's sorted cloud, [start, end),
+ * in ascending order and maximal (two runs of a row never touch).  Position p is original
+ * point perm[p] (octree_export).  The paper's form lists each wholly contained octant as
+ * one range and each other neighbour alone; the maximal runs merge adjacent entries of
+ * that list, so they are never more, and they depend on the neighbour set only. */
+typedef struct {
+    int64_t n_rows;
+    int64_t n_runs;
+    int64_t* run_ptr; /* device, n_rows + 1: row i's runs are run_ptr[i] .. run_ptr[i + 1] - 1 */
+    int32_t* runs;    /* device, 2 * n_runs int32: start, end of every run */
+} sfc_ranges;
+
+/* radius_search with the range output; same arguments, centres and errors.  Allocates the
+ * output (release with sfc_ranges_free); synchronises cuda_stream as radius_search. */
+sfc_status radius_search_ranges(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                                void* cuda_stream, sfc_ranges* out);
+sfc_status sfc_ranges_free(sfc_ranges* ranges, void* cuda_stream);
+
 /* k nearest neighbours (section 3.3) under the squared Euclidean distance in binary32,
  * d2 = (dx*dx + dy*dy) + dz*dz with d = p - c, each operation rounded to nearest.
  *   queries_xyz  as for radius_search (NULL = all tree points, original order).

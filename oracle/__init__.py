@@ -15,6 +15,8 @@ names the passage of the paper it follows:
 * section 3.1 pointer octree: :class:`PointerOctree`
 * section 3.2 kernels:      :func:`pred`, :func:`radius_brute`, :meth:`PointerOctree.radius`
 * section 3.3 kNN:          :func:`knn_brute`, :meth:`PointerOctree.knn`
+* section 5.1 range output: :func:`runs_of_rows`, :meth:`Pipeline.radius_runs`,
+  :meth:`Pipeline.neighbours_struct`
 * section 5.2 histogram:    :func:`locality_histogram`
 """
 from __future__ import annotations
@@ -289,6 +291,24 @@ def locality_histogram(nbr_pos, row_pos, n: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- whole pipeline
+# ----------------------------------------------------------------------------- section 5.1 range output
+def runs_of_rows(row_ptr, positions) -> tuple[np.ndarray, np.ndarray]:
+    """Every row's neighbours, given as ascending sorted positions, as the maximal runs
+    [start, end) of consecutive positions (run_ptr[rows + 1], runs[n_runs, 2])."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    pos = np.asarray(positions, dtype=np.int64)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    new = np.ones(len(pos), bool)
+    if len(pos) > 1:
+        new[1:] = (rows[1:] != rows[:-1]) | (pos[1:] != pos[:-1] + 1)
+    first = np.flatnonzero(new)
+    last = np.append(first[1:], len(pos)) - 1
+    runs = np.stack([pos[first], pos[last] + 1], axis=1) if len(pos) else np.zeros((0, 2), np.int64)
+    run_ptr = np.zeros(len(rp), np.int64)
+    np.add.at(run_ptr, rows[first] + 1, 1)
+    return np.cumsum(run_ptr), runs
+
+
 class Pipeline:
     """The full reference pipeline for one cloud: bbox, cells, codes, order, leaves, tree."""
 
@@ -309,6 +329,56 @@ class Pipeline:
     def nodes(self) -> dict:
         tree_enc = ENC_MORTON if self.enc == ENC_NONE else self.enc
         return self.tree.nodes(tree_enc, self.perm, self.sorted_keys)
+
+    def radius_runs(self, queries, r: float, kern: int, nthreads: int = 0):
+        """The range output of the fixed-radius search: every row's neighbours (the naive
+        octree search) as maximal runs of consecutive sorted positions."""
+        rp, cols = self.tree.radius(queries, r, kern, nthreads)
+        pos = self.rank[self.rows_by_rank(rp, cols).astype(np.int64)]
+        return runs_of_rows(rp, pos)
+
+    def neighbours_struct(self, centre, r: float, kern: int) -> list:
+        """Section 5.1 neighboursStruct for one centre, step by step on the pointer octree:
+        a branch wholly inside the kernel contributes its index range (step 1a with the
+        range insertion), a disjoint branch is pruned (1b), any other branch is searched
+        (1c); a leaf contributes each point inside the kernel (step 2).  Containment and
+        disjointness are decided on the node's tight box: the corner farthest from the
+        centre inside the kernel, the point of the box nearest to it outside.  Returns the
+        (start, end) entries in walk order (sorted positions)."""
+        if not hasattr(self, "_node_index"):
+            nd = self.nodes()
+            self._nodes = nd
+            self._node_index = {(int(k), int(l)): i for i, (k, l) in enumerate(zip(nd["key"], nd["level"]))}
+        nd, index = self._nodes, self._node_index
+        c = np.asarray(centre, dtype=np.float32)
+        out = []
+
+        def visit(i):
+            if nd["count"][i] == 0:
+                return
+            start, end = int(nd["start"][i]), int(nd["end"][i])
+            if nd["is_leaf"][i]:
+                for p in range(start, end):
+                    if pred(kern, self.xyz[self.perm[p]], c, r):
+                        out.append((p, p + 1))
+                return
+            lo, hi = nd["box"][i, :3], nd["box"][i, 3:]
+            far = np.where(np.abs(hi - c) >= np.abs(lo - c), hi, lo).astype(np.float32)
+            near = np.minimum(np.maximum(c, lo), hi).astype(np.float32)
+            if pred(kern, far, c, r):
+                out.append((start, end))
+                return
+            if not pred(kern, near, c, r):
+                return
+            level = int(nd["level"][i])
+            shift = 3 * (L - level - 1)
+            for digit in range(8):
+                j = index.get((int(nd["key"][i]) + (digit << shift), level + 1))
+                if j is not None:
+                    visit(j)
+
+        visit(index[(0, 0)])
+        return out
 
     def rows_by_rank(self, row_ptr, cols) -> np.ndarray:
         """Reorder every row by the sorted position of its points (the CUDA path's row order)."""

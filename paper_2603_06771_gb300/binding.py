@@ -16,6 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
+    "radius_search_ranges",
     "Batch", "batch_search", "BatchPlan", "batch_autotune", "Server",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
@@ -73,6 +74,9 @@ _SIGNATURES = {
     "octree_export_nodes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     "sfc_encode_cells": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "radius_search_ranges": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int, C.c_void_p,
+                                       C.c_void_p]),
+    "sfc_ranges_free": (C.c_int, [C.c_void_p, C.c_void_p]),
     "batch_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
@@ -290,6 +294,39 @@ def radius_search_csr(tree: Octree, queries: torch.Tensor | None, r: float, kern
     row_ptr = torch.as_tensor(_DeviceArray(owner, csr.row_ptr, csr.n_rows + 1, "<i8"), device="cuda")
     cols = torch.as_tensor(_DeviceArray(owner, csr.cols, csr.nnz, "<i4"), device="cuda")
     return row_ptr, cols
+
+
+class _Ranges(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("n_runs", C.c_int64), ("run_ptr", C.c_void_p), ("runs", C.c_void_p)]
+
+
+class _RangesOwner:
+    def __init__(self, ranges: _Ranges, stream: int):
+        self.ranges = ranges
+        self.stream = stream
+
+    def __del__(self):
+        try:
+            lib().sfc_ranges_free(C.byref(self.ranges), C.c_void_p(self.stream))
+        except Exception:
+            pass
+
+
+def radius_search_ranges(tree: Octree, queries: torch.Tensor | None, r: float, kernel="sphere", stream=None):
+    """``radius_search_ranges`` of the C ABI: (run_ptr int64 [rows + 1], runs int32 [n_runs, 2])
+    of [start, end) sorted positions, library-allocated, viewed as torch tensors."""
+    q = _xyz(queries, "queries")
+    rows = tree.n if q is None else q.shape[0]
+    rg = _Ranges()
+    s = _stream(stream)
+    _check(lib().radius_search_ranges(tree.handle, _ptr(q), 0 if q is None else rows, C.c_float(r), _kern(kernel),
+                                      C.c_void_p(s), C.byref(rg)), "radius_search_ranges")
+    owner = _RangesOwner(rg, s)
+    run_ptr = torch.as_tensor(_DeviceArray(owner, rg.run_ptr, rg.n_rows + 1, "<i8"), device="cuda")
+    if rg.n_runs == 0:
+        return run_ptr, torch.empty((0, 2), dtype=torch.int32, device="cuda")
+    runs = torch.as_tensor(_DeviceArray(owner, rg.runs, 2 * rg.n_runs, "<i4"), device="cuda").view(-1, 2)
+    return run_ptr, runs
 
 
 def knn(tree: Octree, queries: torch.Tensor | None, k: int, stream=None):

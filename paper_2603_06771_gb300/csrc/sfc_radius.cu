@@ -49,6 +49,8 @@ struct RadiusArgs {
     uint32_t* counts;                   // count pass: neighbours per row
     const int64_t* row_ptr;             // fill pass
     int32_t* cols;
+    int2* runs;                         // range output: [start, end) sorted positions per run
+    int out_runs;                       // 1: range output (count runs / write runs)
     unsigned int* err;                  // kGuardTripped is or-ed in when a guard fails
     int64_t max_steps;                  // nodes of the tree: a walk pops each node once at most
     // hit-mask records: mode 1 = this count pass records them, 2 = this fill pass replays
@@ -110,7 +112,12 @@ __device__ __forceinline__ NodeBox shfl_box(const NodeBox& b, int src) {
 // pop reads shared memory only.  An expansion loads the eight children once (lanes 0-7),
 // drops those no centre of the group can reach, and classifies the rest for every lane.
 // Leaf points are staged in shared memory with one coalesced load per 32-point chunk.
-template <int KERN, bool FILL>
+// RUNS: the range output (neighboursStruct, section 5.1): each row lists its neighbours as
+// maximal runs [start, end) of consecutive sorted positions instead of one id each; the
+// count pass counts runs, the fill writes them.
+constexpr uint32_t kNoRun = 0xffffffffu;
+
+template <int KERN, bool FILL, bool RUNS>
 __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(RadiusArgs a) {
     constexpr int kRadiusWarps = radius_warps<FILL>();
     __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
@@ -147,8 +154,32 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
     bool guard_ok = true;
 
     // ---- emitting (shared by the walk and the replay)
+    // range output: the lane's open run [run_s, run_e); positions arrive in ascending order
+    uint32_t run_s = 0, run_e = kNoRun;
+    auto flush_run = [&]() {
+        if (out < out_end) a.runs[out] = make_int2(static_cast<int>(run_s), static_cast<int>(run_e));
+        else guard_ok = false;
+        ++out;
+    };
+    auto add_run = [&](uint32_t s0, uint32_t e0) {
+        if (s0 == run_e) {
+            run_e = e0;
+            return;
+        }
+        if (FILL && run_e != kNoRun) flush_run();
+        run_s = s0;
+        run_e = e0;
+        ++count;
+    };
+    auto finish_runs = [&]() {
+        if (RUNS && FILL && run_e != kNoRun) flush_run();
+    };
     // the lanes of `whole` take [start, end) (step 1a)
     auto take_range = [&](unsigned int whole, uint32_t start, uint32_t end, bool mine) {
+        if (RUNS) {
+            if (mine) add_run(start, end);
+            return;
+        }
         if (FILL) {
             unsigned int todo = whole;
             while (todo) {
@@ -169,8 +200,28 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
             out += end - start;
         }
     };
-    // the hits of a leaf chunk: lane i's row gets the ids (my_id of lane j) of its mask's bits
-    auto take_hits = [&](uint32_t hits, int32_t my_id) {
+    // the hits of a leaf chunk at positions base + t: lane i's row gets the ids (my_id of
+    // lane j) of its mask's bits, or their runs
+    auto take_hits = [&](uint32_t hits, int32_t my_id, uint32_t base) {
+        if (RUNS) {
+            if (!FILL) {  // count runs: starts of runs of ones, the first may extend the open run
+                if (hits) {
+                    count += __popc(hits & ~(hits << 1));
+                    if ((hits & 1u) && base == run_e) --count;
+                    run_e = base + 32u - static_cast<uint32_t>(__clz(hits));
+                }
+                return;
+            }
+            uint32_t m = hits;
+            while (m) {
+                const int s0 = __ffs(m) - 1;
+                const uint32_t rest = ~(m >> s0);  // zeros where the run of ones continues
+                const int len = rest ? __ffs(rest) - 1 : 32 - s0;
+                add_run(base + s0, base + s0 + len);
+                m = s0 + len >= 32 ? 0u : (m & (~0u << (s0 + len)));
+            }
+            return;
+        }
         count += __popc(hits);
         if (FILL) {
             if (out + __popc(hits) > out_end) {  // never true when the count pass agrees
@@ -200,10 +251,11 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
                 if (hd.y & kRangeBit) {
                     take_range(__ballot_sync(0xffffffffu, mask != 0), hd.x, hd.y & ~kRangeBit, mask != 0);
                 } else {
-                    const int32_t my_id = lane < hd.y ? static_cast<int32_t>(a.perm[hd.x + lane]) : 0;
-                    take_hits(mask, my_id);
+                    const int32_t my_id = (!RUNS && lane < hd.y) ? static_cast<int32_t>(a.perm[hd.x + lane]) : 0;
+                    take_hits(mask, my_id, hd.x);
                 }
             }
+            finish_runs();
             if (!guard_ok) atomicOr(a.err, kGuardTripped);
             return;
         }
@@ -333,17 +385,18 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(Radi
                 __syncwarp();
                 if (!need) hits = 0;
                 if (recording && __ballot_sync(0xffffffffu, hits != 0)) record(base, m, hits);
-                take_hits(hits, static_cast<int32_t>(__float_as_uint(mine.w)));
+                take_hits(hits, static_cast<int32_t>(__float_as_uint(mine.w)), base);
             }
         }
     }
+    finish_runs();
     if (!FILL && active) a.counts[row] = count;
     if (recording && lane == 0) a.rec_count[group] = rec_overflow ? kRecordsOverflow : nrec;
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
 }
 
 // One centre per thread, its own depth-first walk; points through the permutation.
-template <int KERN, bool FILL>
+template <int KERN, bool FILL, bool RUNS>
 __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
     const int64_t qi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (qi >= a.nq) return;
@@ -357,6 +410,21 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
     int64_t out = FILL ? a.row_ptr[row] : 0;
     const int64_t out_end = FILL ? a.row_ptr[row + 1] : 0;
     bool guard_ok = true;
+    uint32_t run_s = 0, run_e = kNoRun;  // range output: the open run
+    auto add_run = [&](uint32_t s0, uint32_t e0) {
+        if (s0 == run_e) {
+            run_e = e0;
+            return;
+        }
+        if (FILL && run_e != kNoRun) {
+            if (out < out_end) a.runs[out] = make_int2(static_cast<int>(run_s), static_cast<int>(run_e));
+            else guard_ok = false;
+            ++out;
+        }
+        run_s = s0;
+        run_e = e0;
+        ++count;
+    };
     for (int64_t steps = 0; sp > 0; ++steps) {
         if (steps >= a.max_steps) {
             guard_ok = false;
@@ -371,6 +439,10 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
         const int32_t fc = a.child[node];
         if (fc >= 0) {
             if (cls == 2) {
+                if (RUNS) {
+                    add_run(start, end);
+                    continue;
+                }
                 if (FILL) {
                     if (out + (end - start) > out_end) {
                         guard_ok = false;
@@ -391,6 +463,10 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
                 const uint32_t id = a.perm[j];
                 const float4 p = a.pts[id];
                 if (kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z), a.r, a.r2)) {
+                    if (RUNS) {
+                        add_run(j, j + 1);
+                        continue;
+                    }
                     if (FILL) {
                         if (out < out_end) a.cols[out++] = static_cast<int32_t>(id);
                         else guard_ok = false;
@@ -400,34 +476,44 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
             }
         }
     }
+    if (RUNS && FILL && run_e != kNoRun) {
+        if (out < out_end) a.runs[out] = make_int2(static_cast<int>(run_s), static_cast<int>(run_e));
+        else guard_ok = false;
+    }
     if (!FILL) a.counts[row] = count;
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
 }
 
-template <bool FILL>
-static sfc_status launch_search(const Octree* t, RadiusArgs& a, int kern, cudaStream_t s) {
+template <bool FILL, bool RUNS>
+static sfc_status launch_search_as(const Octree* t, RadiusArgs& a, int kern, cudaStream_t s) {
     if (a.nq == 0) return SFC_OK;
-    const char* name = FILL ? "radius_fill" : "radius_count";
+    const char* name = RUNS ? (FILL ? "radius_ranges_fill" : "radius_ranges_count")
+                            : (FILL ? "radius_fill" : "radius_count");
     if (t->enc == SFC_ENC_NONE) {
         const unsigned int grid = grid_for(a.nq, 128);
         switch (kern) {
-        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SPHERE, FILL>), grid, 128, 0, a); break;
-        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CIRCLE, FILL>), grid, 128, 0, a); break;
-        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CUBE, FILL>), grid, 128, 0, a); break;
-        default: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SQUARE, FILL>), grid, 128, 0, a); break;
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SPHERE, FILL, RUNS>), grid, 128, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CIRCLE, FILL, RUNS>), grid, 128, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CUBE, FILL, RUNS>), grid, 128, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SQUARE, FILL, RUNS>), grid, 128, 0, a); break;
         }
     } else {
         constexpr int kWarps = radius_warps<FILL>();
         const int64_t groups = a.ngroups;
         const unsigned int grid = grid_for(groups, kWarps);
         switch (kern) {
-        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL>), grid, kWarps * 32, 0, a); break;
-        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, FILL>), grid, kWarps * 32, 0, a); break;
-        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, FILL>), grid, kWarps * 32, 0, a); break;
-        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, FILL>), grid, kWarps * 32, 0, a); break;
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, FILL, RUNS>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, FILL, RUNS>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, FILL, RUNS>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, FILL, RUNS>), grid, kWarps * 32, 0, a); break;
         }
     }
     return SFC_OK;
+}
+
+template <bool FILL>
+static sfc_status launch_search(const Octree* t, RadiusArgs& a, int kern, cudaStream_t s) {
+    return a.out_runs ? launch_search_as<FILL, true>(t, a, kern, s) : launch_search_as<FILL, false>(t, a, kern, s);
 }
 
 static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, float r) {
@@ -456,6 +542,8 @@ static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, flo
     a.ngroups = (rows + 31) / 32;
     a.skip = nullptr;
     a.skip_mask = 0;
+    a.runs = nullptr;
+    a.out_runs = 0;
     return a;
 }
 
@@ -506,7 +594,7 @@ static void setup_records(Octree* t, int64_t rows, float r, int kern, cudaStream
 
 static sfc_status count_impl(Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
                              Scratch& scratch, int64_t* row_ptr, const unsigned int* bad, int64_t* nnz,
-                             bool all_points) {
+                             bool all_points, bool runs = false) {
     if (!(r > 0.f) || rows == 0 || t->n == 0) {
         SFC_CUDA(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (rows + 1), s));
     } else {
@@ -514,6 +602,7 @@ static sfc_status count_impl(Octree* t, const float4* q4, int64_t rows, float r,
         SFC_TRY(scratch.alloc(&counts, rows));
         RadiusArgs a = make_args(t, q4, rows, r);
         a.counts = counts;
+        a.out_runs = runs ? 1 : 0;
         if (all_points) setup_records(t, rows, r, kern, s, a);
         const sfc_status st = launch_search<false>(t, a, kern, s);
         if (st != SFC_OK) {
@@ -552,11 +641,13 @@ sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_
 }
 
 static sfc_status fill_impl(Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
-                            const int64_t* row_ptr, int32_t* cols, bool all_points) {
+                            const int64_t* row_ptr, int32_t* cols, bool all_points, int2* runs = nullptr) {
     if (!(r > 0.f) || rows == 0 || t->n == 0) return SFC_OK;
     RadiusArgs a = make_args(t, q4, rows, r);
     a.row_ptr = row_ptr;
     a.cols = cols;
+    a.runs = runs;
+    a.out_runs = runs ? 1 : 0;
     const RadiusRecords& rec = t->records;
     uint32_t rb, qb;
     memcpy(&rb, &rec.r, sizeof rb);
@@ -629,19 +720,19 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
         constexpr int kWarps = radius_warps<true>();
         const unsigned int grid = grid_for(ngroups, kWarps);
         switch (kern) {
-        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, true>), grid, kWarps * 32, 0, a); break;
-        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, true>), grid, kWarps * 32, 0, a); break;
-        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, true>), grid, kWarps * 32, 0, a); break;
-        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, true>), grid, kWarps * 32, 0, a); break;
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, true, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, true, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, true, false>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, true, false>), grid, kWarps * 32, 0, a); break;
         }
     } else {
         constexpr int kWarps = radius_warps<false>();
         const unsigned int grid = grid_for(ngroups, kWarps);
         switch (kern) {
-        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, false>), grid, kWarps * 32, 0, a); break;
-        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, false>), grid, kWarps * 32, 0, a); break;
-        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, false>), grid, kWarps * 32, 0, a); break;
-        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, false, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, false, false>), grid, kWarps * 32, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, false, false>), grid, kWarps * 32, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, false, false>), grid, kWarps * 32, 0, a); break;
         }
     }
     return SFC_OK;
@@ -723,6 +814,57 @@ sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queri
     out->nnz = nnz;
     out->row_ptr = row_ptr;
     out->cols = cols;
+    return SFC_OK;
+}
+
+sfc_status radius_search_ranges(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
+                                void* cuda_stream, sfc_ranges* out) {
+    if (!out) return SFC_ERR_INVALID;
+    out->n_rows = 0;
+    out->n_runs = 0;
+    out->run_ptr = nullptr;
+    out->runs = nullptr;
+    int64_t rows = 0;
+    SFC_TRY(sfc::check_radius_args(h, queries_xyz, n_queries, r, kern, &rows));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc_status st;
+    int64_t n_runs = 0;
+    int64_t* run_ptr = nullptr;
+    int2* runs = nullptr;
+    {
+        sfc::Scratch scratch(s);
+        const float4* q4 = nullptr;
+        unsigned int* bad = nullptr;
+        st = sfc::prepare(&h->tree, queries_xyz, rows, s, scratch, &q4, &bad);
+        if (st == SFC_OK) st = sfc::dev_alloc(&run_ptr, rows + 1, s);
+        const bool all = queries_xyz == nullptr;
+        if (st == SFC_OK)
+            st = sfc::count_impl(&h->tree, q4, rows, r, kern, s, scratch, run_ptr, bad, &n_runs, all, true);
+        if (st == SFC_OK) st = sfc::dev_alloc(&runs, n_runs, s);
+        if (st == SFC_OK) st = sfc::fill_impl(&h->tree, q4, rows, r, kern, s, run_ptr, nullptr, all, runs);
+        if (st == SFC_OK) st = sfc::check_guard(&h->tree, s);
+    }
+    if (st != SFC_OK) {
+        sfc::dev_free(run_ptr, s);
+        sfc::dev_free(runs, s);
+        return st;
+    }
+    out->n_rows = rows;
+    out->n_runs = n_runs;
+    out->run_ptr = run_ptr;
+    out->runs = reinterpret_cast<int32_t*>(runs);
+    return SFC_OK;
+}
+
+sfc_status sfc_ranges_free(sfc_ranges* ranges, void* cuda_stream) {
+    if (!ranges) return SFC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    sfc::dev_free(ranges->run_ptr, s);
+    sfc::dev_free(ranges->runs, s);
+    ranges->run_ptr = nullptr;
+    ranges->runs = nullptr;
+    ranges->n_rows = 0;
+    ranges->n_runs = 0;
     return SFC_OK;
 }
 

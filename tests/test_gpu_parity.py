@@ -276,3 +276,53 @@ def test_errors_are_reported():
     assert st == 6
     with pytest.raises(KeyError):
         sfc.radius_search(t, None, 0.1, "ellipse")
+
+
+# ----------------------------------------------------------------------------- range output (neighboursStruct)
+@pytest.mark.parametrize("enc", ENCS)
+@pytest.mark.parametrize("name,ncap,r", [("uniform131k", 32, 0.04), ("lidar60k", 32, 2.0), ("lattice", 4, 2.5),
+                                         ("duplicates", 8, 0.05), ("clusters40k", 16, 1.5)])
+def test_radius_ranges_all_points(name, ncap, r, enc):
+    p = oracle_pipeline(name, enc, ncap)
+    t = sfc.octree_build(dev(p.xyz), enc, leaf_capacity=ncap)
+    for kern in KERNS:
+        rr = r if kern in ("sphere", "cube") else r * 0.6
+        orp, oruns = p.radius_runs(p.xyz, rr, KERN[kern])
+        rp, runs = sfc.radius_search_ranges(t, None, rr, kern)
+        assert np.array_equal(rp.cpu().numpy(), orp), kern
+        assert np.array_equal(runs.cpu().numpy().astype(np.int64), oruns), kern
+        # the runs expand to the CSR of radius_search through the permutation
+        crp, ccols = gpu_csr(*sfc.radius_search(t, None, rr, kern))
+        perm = t.export()["perm"].cpu().numpy()
+        lens = oruns[:, 1] - oruns[:, 0]
+        run_rows = np.repeat(np.arange(len(orp) - 1), np.diff(orp))
+        row_len = np.bincount(run_rows, weights=lens, minlength=len(orp) - 1).astype(np.int64)
+        assert np.array_equal(np.diff(crp), row_len), kern
+        expanded = np.arange(lens.sum()) - np.repeat(np.cumsum(lens) - lens, lens) + np.repeat(oruns[:, 0], lens)
+        assert np.array_equal(perm[expanded], ccols), kern
+        assert len(oruns) <= len(ccols)
+
+
+@pytest.mark.parametrize("enc", ENCS)
+def test_radius_ranges_caller_centres(enc):
+    name, ncap, r = "lidar60k", 32, 3.0
+    p = oracle_pipeline(name, enc, ncap)
+    q = _centres(p.xyz, 1007, 29)
+    t = sfc.octree_build(dev(p.xyz), enc, leaf_capacity=ncap)
+    for kern in KERNS:
+        orp, oruns = p.radius_runs(q, r, KERN[kern])
+        rp, runs = sfc.radius_search_ranges(t, dev(q), r, kern)
+        assert np.array_equal(rp.cpu().numpy(), orp), kern
+        assert np.array_equal(runs.cpu().numpy().astype(np.int64), oruns), kern
+
+
+def test_radius_ranges_special_cases():
+    t = sfc.octree_build(dev(cloud("empty")), "hilbert")
+    rp, runs = sfc.radius_search_ranges(t, None, 1.0, "sphere")
+    assert rp.cpu().tolist() == [0] and runs.shape == (0, 2)
+    xyz = cloud("identical")  # every point at one place: one run of all 100 positions per row
+    t = sfc.octree_build(dev(xyz), "morton", leaf_capacity=8)
+    rp, runs = sfc.radius_search_ranges(t, None, 0.5, "cube")
+    assert (np.diff(rp.cpu().numpy()) == 1).all() and (runs.cpu().numpy() == [0, 100]).all()
+    rp, runs = sfc.radius_search_ranges(t, None, 0.0, "sphere")
+    assert (rp.cpu().numpy() == 0).all() and runs.shape == (0, 2)

@@ -303,6 +303,59 @@ def test_knn_rows_are_exact_and_sorted():
         assert np.allclose(dd[idx[i]], d2[i], rtol=1e-5, atol=1e-12)
 
 
+# ----------------------------------------------------------------------------- section 5.1 range output
+def _merge(entries):
+    out = []
+    for s0, e0 in entries:
+        if out and out[-1][1] == s0:
+            out[-1] = (out[-1][0], e0)
+        else:
+            out.append((s0, e0))
+    return out
+
+
+def test_runs_of_rows_hand_example():
+    # rows: {3,4,5,9,11,12}, {}, {7}, {0,1}
+    rp = np.array([0, 6, 6, 7, 9])
+    pos = np.array([3, 4, 5, 9, 11, 12, 7, 0, 1])
+    run_ptr, runs = oracle.runs_of_rows(rp, pos)
+    assert run_ptr.tolist() == [0, 3, 3, 4, 5]
+    assert runs.tolist() == [[3, 6], [9, 10], [11, 13], [7, 8], [0, 2]]
+
+
+@pytest.mark.parametrize("gen", ["uniform", "lattice", "lidar"])
+def test_neighbours_struct_merges_to_the_runs(gen):
+    """The paper's neighboursStruct walk (octant ranges + single points), with adjacent
+    entries merged, is the run encoding of the exact neighbour set; large radii make it
+    take whole octants."""
+    if gen == "uniform":
+        xyz = synth.uniform_cube(2500, 61)
+        radii = (0.05, 0.2, 0.45)
+    elif gen == "lattice":
+        g = np.arange(9, dtype=np.float32)
+        xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).copy()
+        radii = (1.0, 2.5, 4.0)
+    else:
+        xyz = synth.lidar_tile(3000, 62, side=float(np.sqrt(300.0)))
+        radii = (0.5, 2.0, 6.0)
+    p = oracle.Pipeline(xyz, oracle.ENC_HILBERT, 8)
+    centres = xyz[::97]
+    took_octant = False
+    for kern in (oracle.SPHERE, oracle.CIRCLE, oracle.CUBE, oracle.SQUARE):
+        for r in radii:
+            run_ptr, runs = p.radius_runs(centres, r, kern)
+            brp, bcols = oracle.radius_brute(xyz, centres, r, kern)
+            for i, c in enumerate(centres):
+                ent = p.neighbours_struct(c, r, kern)
+                took_octant |= any(e - s0 > 1 for s0, e in ent)
+                want = [tuple(x) for x in runs[run_ptr[i]:run_ptr[i + 1]].tolist()]
+                assert _merge(ent) == want
+                assert len(ent) >= len(want)
+                expanded = np.concatenate([np.arange(s0, e0) for s0, e0 in want]) if want else np.zeros(0, int)
+                assert np.array_equal(np.sort(p.perm[expanded]), np.sort(bcols[brp[i]:brp[i + 1]]))
+    assert took_octant
+
+
 # ----------------------------------------------------------------------------- section 5.2 histogram
 def test_locality_histogram_properties():
     """H_k(0) = N and sum_d H_k(d) = kN for distinct points (section 5.2)."""
