@@ -297,6 +297,29 @@ sfc_status batch_plan_result(sfc_batch_plan p, int32_t cloud, const int64_t** ro
 /* Release the plan (waits for cuda_stream first). */
 sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream);
 
+/* ---- section 5.2: kNN locality histogram ------------------------------------------ */
+
+/* H_k and its skewness for a set of centres (cloud points, by original index; a 1 % subset
+ * estimates the whole cloud's): the centres' k nearest neighbours come from this octree's
+ * search; `order` gives every point a storage position (SFC_ENC_NONE: its original index;
+ * SFC_ENC_MORTON / SFC_ENC_HILBERT: its rank in the stable order of that curve's codes
+ * under this octree's discretisation, equal codes by original index); H_k(d) counts the
+ * (centre, neighbour) pairs whose positions are d apart.
+ *   hist  device, n_points uint64 (H_k(0 .. n - 1)), or NULL for G1 only.
+ *   g1    host: the Fisher-Pearson skewness E[((d - mu) / sigma)^3] of that distribution
+ *         (float64, mean first, then central moments); 0 when sigma = 0.
+ * Neighbour slots padded for k > n are skipped.  Errors: SFC_ERR_INVALID (bad argument or
+ * a centre id outside the cloud), SFC_ERR_TOO_LARGE (k > 64), SFC_ERR_NOT_DEVICE_PTR.
+ * Synchronises cuda_stream. */
+sfc_status knn_locality(sfc_octree h, const int32_t* centre_ids, int64_t n_centres, int32_t k, sfc_encoding order,
+                        void* cuda_stream, uint64_t* hist, double* g1);
+
+/* The storage order with the largest G1 for these centres (the paper's selection rule:
+ * the most left-heavy histogram), among input order, Morton and Hilbert; g1_by_order
+ * (host, 3 doubles, may be NULL) receives G1 for NONE, MORTON, HILBERT. */
+sfc_status choose_encoding(sfc_octree h, const int32_t* centre_ids, int64_t n_centres, int32_t k, void* cuda_stream,
+                           sfc_encoding* best, double* g1_by_order);
+
 /* ---- serving: requests that arrive at any time ------------------------------------ */
 
 typedef struct sfc_server_s* sfc_server; /* owned by the library */

@@ -290,7 +290,21 @@ def locality_histogram(nbr_pos, row_pos, n: int) -> np.ndarray:
     return hist
 
 
-# ----------------------------------------------------------------------------- whole pipeline
+def skewness(hist) -> float:
+    """Section 5.2: the Fisher-Pearson coefficient G1 = E[((d - mu) / sigma)^3] of the
+    distribution with frequencies hist[d], d = 0, 1, ... (float64; 0 when sigma = 0)."""
+    h = np.asarray(hist, dtype=np.float64)
+    d = np.arange(len(h), dtype=np.float64)
+    w = h.sum()
+    if w == 0:
+        return 0.0
+    mu = (h * d).sum() / w
+    x = d - mu
+    m2 = (h * x * x).sum() / w
+    m3 = (h * x * x * x).sum() / w
+    return float(m3 / m2 ** 1.5) if m2 > 0 else 0.0
+
+
 # ----------------------------------------------------------------------------- section 5.1 range output
 def runs_of_rows(row_ptr, positions) -> tuple[np.ndarray, np.ndarray]:
     """Every row's neighbours, given as ascending sorted positions, as the maximal runs
@@ -309,6 +323,7 @@ def runs_of_rows(row_ptr, positions) -> tuple[np.ndarray, np.ndarray]:
     return np.cumsum(run_ptr), runs
 
 
+# ----------------------------------------------------------------------------- whole pipeline
 class Pipeline:
     """The full reference pipeline for one cloud: bbox, cells, codes, order, leaves, tree."""
 
@@ -379,6 +394,23 @@ class Pipeline:
 
         visit(index[(0, 0)])
         return out
+
+    def locality(self, centre_ids, k: int, order: int):
+        """Section 5.2: H_k of the given centres (original ids) and its skewness G1, with
+        the storage positions of `order` (ENC_NONE: original index; a curve: rank in the
+        stable order of its codes of this cloud's cells)."""
+        ids = np.asarray(centre_ids, dtype=np.int64)
+        nbr, _ = self.tree.knn(self.xyz[ids], k)
+        if order == ENC_NONE:
+            rank = np.arange(len(self.xyz), dtype=np.int64)
+        else:
+            perm, _ = sort_keys(encode_cells(self.cell, order))
+            rank = np.empty(len(perm), np.int64)
+            rank[perm.astype(np.int64)] = np.arange(len(perm))
+        nb = nbr.astype(np.int64)
+        pos = np.where(nb >= 0, rank[np.maximum(nb, 0)], -1)
+        hist = locality_histogram(pos, rank[ids], len(self.xyz))
+        return hist, skewness(hist)
 
     def rows_by_rank(self, row_ptr, cols) -> np.ndarray:
         """Reorder every row by the sorted position of its points (the CUDA path's row order)."""

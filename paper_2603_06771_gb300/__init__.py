@@ -7,12 +7,12 @@ with ``batch_search``, ``BatchPlan`` (a recorded CUDA graph) and ``batch_autotun
 arriving over time with ``Server``.
 """
 from .binding import (ENCODINGS, KERNELS, Batch, BatchPlan, Octree, Server, SFCError, batch_autotune,
-                      batch_search, encode_cells, knn, launch_count, library_path, octree_build, profile_enable,
-                      profile_read, radius_count, radius_fill, radius_search, radius_search_csr,
-                      radius_search_ranges)
+                      batch_search, choose_encoding, encode_cells, knn, knn_locality, launch_count, library_path,
+                      octree_build, profile_enable, profile_read, radius_count, radius_fill, radius_search,
+                      radius_search_csr, radius_search_ranges)
 from .build import build
 
 __all__ = ["ENCODINGS", "KERNELS", "Batch", "BatchPlan", "Octree", "Server", "SFCError", "batch_autotune",
-           "batch_search", "build", "encode_cells", "knn", "launch_count", "library_path", "octree_build",
-           "profile_enable", "profile_read", "radius_count", "radius_fill", "radius_search", "radius_search_csr",
-           "radius_search_ranges"]
+           "batch_search", "build", "choose_encoding", "encode_cells", "knn", "knn_locality", "launch_count",
+           "library_path", "octree_build", "profile_enable", "profile_read", "radius_count", "radius_fill",
+           "radius_search", "radius_search_csr", "radius_search_ranges"]

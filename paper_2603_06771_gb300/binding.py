@@ -16,7 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
-    "radius_search_ranges",
+    "radius_search_ranges", "knn_locality", "choose_encoding",
     "Batch", "batch_search", "BatchPlan", "batch_autotune", "Server",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
@@ -77,6 +77,9 @@ _SIGNATURES = {
     "radius_search_ranges": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int, C.c_void_p,
                                        C.c_void_p]),
     "sfc_ranges_free": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "knn_locality": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    "choose_encoding": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "batch_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
@@ -327,6 +330,34 @@ def radius_search_ranges(tree: Octree, queries: torch.Tensor | None, r: float, k
         return run_ptr, torch.empty((0, 2), dtype=torch.int32, device="cuda")
     runs = torch.as_tensor(_DeviceArray(owner, rg.runs, 2 * rg.n_runs, "<i4"), device="cuda").view(-1, 2)
     return run_ptr, runs
+
+
+def _ids(centre_ids: torch.Tensor) -> torch.Tensor:
+    if not (isinstance(centre_ids, torch.Tensor) and centre_ids.is_cuda and centre_ids.dim() == 1):
+        raise ValueError("centre_ids must be a 1-D CUDA tensor")
+    return centre_ids.to(torch.int32).contiguous()
+
+
+def knn_locality(tree: Octree, centre_ids: torch.Tensor, k: int, order="hilbert", histogram: bool = True,
+                 stream=None):
+    """``knn_locality`` of the C ABI: (H_k as an int64 CUDA tensor of n entries or None, G1)."""
+    ids = _ids(centre_ids)
+    hist = torch.zeros(max(tree.n, 1), dtype=torch.int64, device="cuda") if histogram else None
+    g1 = C.c_double()
+    _check(lib().knn_locality(tree.handle, _ptr(ids), ids.shape[0], int(k), _enc(order), C.c_void_p(_stream(stream)),
+                              _ptr(hist) if hist is not None else None, C.byref(g1)), "knn_locality")
+    return (hist[:tree.n] if hist is not None else None), g1.value
+
+
+def choose_encoding(tree: Octree, centre_ids: torch.Tensor, k: int, stream=None):
+    """``choose_encoding`` of the C ABI: (name of the order with the largest G1, {order: G1})."""
+    ids = _ids(centre_ids)
+    best = C.c_int()
+    g = (C.c_double * 3)()
+    _check(lib().choose_encoding(tree.handle, _ptr(ids), ids.shape[0], int(k), C.c_void_p(_stream(stream)),
+                                 C.byref(best), g), "choose_encoding")
+    names = {v: k for k, v in ENCODINGS.items()}
+    return names[best.value], {"none": g[0], "morton": g[1], "hilbert": g[2]}
 
 
 def knn(tree: Octree, queries: torch.Tensor | None, k: int, stream=None):

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsfcoct.so")
-SOURCES = ["sfc_runtime.cu", "sfc_build.cu", "sfc_radius.cu", "sfc_knn.cu", "sfc_static.cu", "sfc_batch.cu", "sfc_serve.cu"]
+SOURCES = ["sfc_runtime.cu", "sfc_build.cu", "sfc_radius.cu", "sfc_knn.cu", "sfc_static.cu", "sfc_batch.cu", "sfc_serve.cu",
+           "sfc_locality.cu"]
 HEADERS = [os.path.join(CSRC, "sfc_internal.cuh"), os.path.join(ROOT, "include", "sfcoct.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 # -fmad=false: no multiply-add contraction anywhere; the distance tests also use

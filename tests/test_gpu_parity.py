@@ -326,3 +326,33 @@ def test_radius_ranges_special_cases():
     assert (np.diff(rp.cpu().numpy()) == 1).all() and (runs.cpu().numpy() == [0, 100]).all()
     rp, runs = sfc.radius_search_ranges(t, None, 0.0, "sphere")
     assert (rp.cpu().numpy() == 0).all() and runs.shape == (0, 2)
+
+
+# ----------------------------------------------------------------------------- locality histogram (section 5.2)
+@pytest.mark.parametrize("enc", ENCS)
+@pytest.mark.parametrize("name,step", [("lidar60k", 100), ("uniform131k", 100), ("duplicates", 7)])
+def test_knn_locality_histogram(name, step, enc):
+    p = oracle_pipeline(name, enc, 32)
+    t = sfc.octree_build(dev(p.xyz), enc, leaf_capacity=32)
+    ids = np.arange(0, len(p.xyz), step, dtype=np.int32)
+    g = {}
+    for order in ENCS:
+        oh, og = p.locality(ids, 8, ENC[order])
+        h, g1 = sfc.knn_locality(t, dev(ids), 8, order)
+        assert np.array_equal(h.cpu().numpy(), oh), order
+        assert abs(g1 - og) <= 1e-9 * max(1.0, abs(og)), order
+        g[order] = og
+    best, gs = sfc.choose_encoding(t, dev(ids), 8)
+    assert best == max(g, key=g.get)
+    for order in ENCS:
+        assert abs(gs[order] - g[order]) <= 1e-9 * max(1.0, abs(g[order]))
+
+
+def test_knn_locality_errors():
+    t = sfc.octree_build(dev(cloud("uniform4097")), "hilbert")
+    with pytest.raises(sfc.SFCError):
+        sfc.knn_locality(t, dev(np.array([0, 4097], np.int32)), 4, "morton")
+    with pytest.raises(sfc.SFCError):
+        sfc.knn_locality(t, dev(np.array([0], np.int32)), 65, "morton")
+    h, g1 = sfc.knn_locality(t, dev(np.zeros(0, np.int32)), 4, "morton")
+    assert g1 == 0.0 and int(h.sum()) == 0

@@ -372,6 +372,36 @@ def test_locality_histogram_properties():
     assert (h * d).sum() < (h_none * d).sum()
 
 
+def test_skewness_matches_library_and_closed_forms():
+    """G1 of section 5.2 against scipy's biased sample skewness on the expanded sample,
+    a symmetric histogram (0) and the two-point (Bernoulli) closed form
+    (1 - 2q) / sqrt(q (1 - q)), q the share at d = 1."""
+    stats = pytest.importorskip("scipy.stats")
+    rng = synth.Rng(71)
+    for t in range(4):
+        h = rng.integers(t, 60, 50).astype(np.int64)
+        d = np.repeat(np.arange(len(h)), h)
+        assert abs(oracle.skewness(h) - stats.skew(d, bias=True)) < 1e-9
+    assert abs(oracle.skewness([1, 4, 6, 4, 1])) < 1e-12
+    for a, b in ((1, 3), (2, 7), (5, 1)):
+        q = b / (a + b)
+        assert abs(oracle.skewness([a, b]) - (1 - 2 * q) / np.sqrt(q * (1 - q))) < 1e-12
+    assert oracle.skewness([0, 0, 5]) == 0.0
+
+
+def test_locality_subset_properties():
+    """H_k of a subset: H_k(0) = centres, sum = k * centres; the curve orders are more
+    left-heavy than the input order (section 5.2, Table 5)."""
+    xyz = synth.lidar_tile(30000, 73, side=float(np.sqrt(3000.0)))
+    p = oracle.Pipeline(xyz, oracle.ENC_HILBERT, 32)
+    ids = np.arange(0, len(xyz), 100)
+    g = {}
+    for order in (oracle.ENC_NONE, oracle.ENC_MORTON, oracle.ENC_HILBERT):
+        h, g[order] = p.locality(ids, 8, order)
+        assert h[0] == len(ids) and h.sum() == 8 * len(ids)
+    assert g[oracle.ENC_MORTON] > g[oracle.ENC_NONE] and g[oracle.ENC_HILBERT] > g[oracle.ENC_NONE]
+
+
 # ----------------------------------------------------------------------------- section 7.5 memory model
 def test_table7_overhead_arithmetic():
     for _, t_o, t_p, rho, omega in read_golden("table7_memory_overhead.txt"):
