@@ -68,6 +68,8 @@ def parse_args(argv=None):
     ap.add_argument("--radius", type=float, default=WORKLOAD["radius"]["r"])
     ap.add_argument("--kernel", choices=["sphere", "circle", "cube", "square"], default=WORKLOAD["radius"]["kernel"])
     ap.add_argument("--k", type=int, default=WORKLOAD["knn_k"])
+    ap.add_argument("--radius-output", choices=["ids", "ranges"], default="ids",
+                    help="neighbour ids (CSR) or runs of sorted positions (range output)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving"], default="lidar_tile_10M")
@@ -164,10 +166,15 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- the step
 def run_step(sfc, pts, cfg):
-    """The whole path once; returns (tree, row_ptr, cols, nnz, idx, d2)."""
+    """The whole path once; returns (tree, row_ptr, cols, nnz, idx, d2).  With the range
+    output, (row_ptr, cols, nnz) are the run pointers, the runs and their number."""
     tree = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
-    row_ptr, nnz = sfc.radius_count(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
-    cols = sfc.radius_fill(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"], row_ptr, nnz)
+    if cfg["radius"].get("output") == "ranges":
+        row_ptr, cols = sfc.radius_search_ranges(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
+        nnz = int(cols.shape[0])
+    else:
+        row_ptr, nnz = sfc.radius_count(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
+        cols = sfc.radius_fill(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"], row_ptr, nnz)
     idx, d2 = sfc.knn(tree, None, cfg["knn_k"])
     return tree, row_ptr, cols, nnz, idx, d2
 
@@ -176,6 +183,8 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
     """Bytes one launch of ``kernel`` must move at minimum (the per-unit figures of the design doc)."""
     table = {
         "radius_fill": 16 * n + 8 * (n + 1) + 4 * nnz,   # points + ids, row pointers, neighbour ids
+        "radius_ranges_fill": 16 * n + 8 * (n + 1) + 8 * nnz,  # points, run pointers, runs (nnz = runs)
+        "radius_ranges_count": 12 * n + 4 * n,
         "radius_count": 12 * n + 4 * n,                  # points, counts
         "knn": 16 * n + 8 * n * k,                       # points + ids, k (id, d2) pairs per centre
         "radix_scatter": 24 * n,                         # read + write (code, index)
@@ -567,6 +576,8 @@ def main(argv=None):
         return serve_main(args)
     cfg = dict(WORKLOAD, leaf_capacity=args.leaf_capacity, encoding=args.encoding, knn_k=args.k,
                radius={"kernel": args.kernel, "r": args.radius})
+    if args.radius_output == "ranges":
+        cfg["radius"]["output"] = "ranges"
     if args.impl == "reference":
         return reference_arm(args, cfg)
 
@@ -657,7 +668,8 @@ def main(argv=None):
     if not args.no_e2e:
         h_xyz = torch.from_numpy(xyz).pin_memory()
         h_rp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
-        h_cols = torch.empty(int(nnz * 1.05) + 1024, dtype=torch.int32, pin_memory=True)
+        per = 2 if cfg["radius"].get("output") == "ranges" else 1  # int32 words per output entry
+        h_cols = torch.empty(per * (int(nnz * 1.05) + 1024), dtype=torch.int32, pin_memory=True)
         h_idx = torch.empty((n, k), dtype=torch.int32, pin_memory=True)
         h_d2 = torch.empty((n, k), dtype=torch.float32, pin_memory=True)
         d_pts = torch.empty_like(pts)
@@ -669,7 +681,7 @@ def main(argv=None):
             d_pts.copy_(h_xyz, non_blocking=True)
             tree, row_ptr, cols, e_nnz, idx, d2 = run_step(sfc, d_pts, cfg)
             h_rp.copy_(row_ptr, non_blocking=True)
-            h_cols[:e_nnz].copy_(cols, non_blocking=True)
+            h_cols[:per * e_nnz].copy_(cols.reshape(-1), non_blocking=True)
             h_idx.copy_(idx, non_blocking=True)
             h_d2.copy_(d2, non_blocking=True)
             b.record(stream)
@@ -680,7 +692,7 @@ def main(argv=None):
                 e_ms.append(a.elapsed_time(b))
         e_total, e_units = aggregate(sum(e_ms), 2.0 * n * args.steps, world, torch.device("cuda", local))
         e2e = {"value": e_units / (e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
-               "d2h_bytes_per_step": 8 * (n + 1) + 4 * nnz + 8 * n * k, "ms_per_step": e_total / args.steps}
+               "d2h_bytes_per_step": 8 * (n + 1) + 4 * per * nnz + 8 * n * k, "ms_per_step": e_total / args.steps}
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:

@@ -204,7 +204,8 @@ typedef struct {
     int32_t k;        /* SFC_SEARCH_KNN: neighbours, 1 <= k <= 64 */
     int32_t leaf_capacity; /* this cloud's leaf capacity; 0 = opts->leaf_capacity */
     int32_t knn_window;    /* SFC_SEARCH_KNN: curve neighbours per side that seed each list,
-                              0..32 (0 = max(16, (k + 1) / 2)); a speed knob only */
+                              0..64 (0 = max(8, k), the default of knn()); a speed knob only
+                              (a window wider than the list size class allows is not used) */
 } sfc_batch_cloud;
 
 typedef struct sfc_batch_s* sfc_batch; /* results of a batch, owned by the library */
@@ -250,7 +251,7 @@ sfc_status batch_free(sfc_batch b, void* cuda_stream);
  * knn_window_out[n_clouds] (0 for radius clouds), ready for sfc_batch_cloud.  Results of a
  * batch do not depend on either knob.  The paper has no counterpart (it fixes N_max per
  * run).  Errors as batch_search, plus SFC_ERR_INVALID for a candidate < 1 or a window
- * above 32.  Synchronises cuda_stream repeatedly. */
+ * above 64.  Synchronises cuda_stream repeatedly. */
 sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
                           const sfc_build_opts* opts, const int32_t* leaf_candidates, int32_t n_leaf,
                           const int32_t* window_candidates, int32_t n_window, void* cuda_stream,

@@ -539,7 +539,7 @@ class BatchPlan(Batch):
 
 
 def batch_autotune(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_capacity: int = 32,
-                   prune: bool = True, leaf_candidates=(16, 32, 64, 128, 256), window_candidates=(16, 24, 32),
+                   prune: bool = True, leaf_candidates=(16, 32, 64, 128, 256), window_candidates=(8, 16, 32, 64),
                    stream=None) -> list:
     """``batch_autotune`` of the C ABI: the clouds with ``leaf_capacity`` and (kNN)
     ``knn_window`` filled in from timing this batch on the device."""

@@ -494,7 +494,7 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
             q.k = c.k;
             q.r = c.r;
             q.r2 = c.r * c.r;
-            q.window = c.knn_window > 0 ? c.knn_window : std::max(16, (c.k + 1) / 2);
+            q.window = c.knn_window > 0 ? c.knn_window : knn_default_window(c.k);
             if (c.search == SFC_SEARCH_RADIUS) {
                 if (c.r > 0.f) {  // r <= 0: every row empty
                     q.row0 = p;
@@ -716,7 +716,7 @@ static sfc_status check_batch_args(const sfc_batch_cloud* clouds, int32_t n_clou
     *total = 0;
     for (int i = 0; i < n_clouds; ++i) {
         const sfc_batch_cloud& c = clouds[i];
-        if (c.n_points < 0 || c.leaf_capacity < 0 || c.knn_window < 0 || c.knn_window > 32) return SFC_ERR_INVALID;
+        if (c.n_points < 0 || c.leaf_capacity < 0 || c.knn_window < 0 || c.knn_window > 64) return SFC_ERR_INVALID;
         if (c.search == SFC_SEARCH_RADIUS) {
             if (c.kernel < 0 || c.kernel > 3 || isnan(c.r)) return SFC_ERR_INVALID;
         } else if (c.search == SFC_SEARCH_KNN) {
@@ -1237,7 +1237,7 @@ sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds
     for (int i = 0; i < n_leaf; ++i)
         if (leaf_candidates[i] < 1) return SFC_ERR_INVALID;
     for (int i = 0; i < n_window; ++i)
-        if (window_candidates[i] < 1 || window_candidates[i] > 32) return SFC_ERR_INVALID;
+        if (window_candidates[i] < 1 || window_candidates[i] > 64) return SFC_ERR_INVALID;
     if (total > 0 && (!points_xyz || !sfc::is_device_ptr(points_xyz))) return SFC_ERR_NOT_DEVICE_PTR;
     int dev = 0;
     SFC_CUDA(cudaGetDevice(&dev));

@@ -402,6 +402,8 @@ struct BatchSeg {
     unsigned int mn[3], mx[3];
     unsigned int bad;
 };
+// curve neighbours per side that seed an all-points kNN list (knn, batches)
+inline int knn_default_window(int k) { return k < 8 ? 8 : k; }
 constexpr int kBatchMax = 1024;  // clouds per batch (segment starts are staged in shared memory)
 
 // codes of a batch, each cloud with its own box and scale (sfc_build.cu)

@@ -242,7 +242,8 @@ __device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
 template <int KMAX>
 __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a) {
     constexpr int kWarps = knn_warps<KMAX>();
-    constexpr int kBuf = 96;  // staged points: the seeding window (3 x 32) or one leaf chunk
+    // staged points: the seeding window (32 + 2 window - 1 positions) or one leaf chunk
+    constexpr int kBuf = KMAX <= 32 ? 96 : 32 + 2 * KMAX;
     __shared__ int4 stack_e[kWarps][kStackDepth];  // first child, start, end, lanes needing it
     __shared__ uint64_t heaps[kWarps][KMAX][32];
     __shared__ float4 pbuf[kWarps][kBuf];
@@ -309,8 +310,9 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a)
     int64_t win_lo = 0;
     uint32_t win_n = 0;
     if (window > 0 && 32 + 2 * window - 1 <= kBuf) {
-        const int64_t r0 = first - (window - 1);  // staged positions r0 .. r0 + 95
-        for (int j = lane; j < kBuf; j += 32) {
+        const int64_t r0 = first - (window - 1);  // staged positions r0 .. r0 + span - 1
+        const int span = 32 + 2 * static_cast<int>(window) - 1;
+        for (int j = lane; j < span; j += 32) {
             const int64_t pos = r0 + j;
             buf[j] = (pos >= q_lo && pos < q_end) ? __ldg(&a.pts[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -620,9 +622,9 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.ngroups = (rows + 31) / 32;
         a.skip = nullptr;
         a.skip_mask = 0;
-        // curve neighbours per side for the seeding window: at least k / 2 so that the k
-        // nearest along the curve fill the heap; the staged span 32 + 2 * window - 1 fits 96
-        a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? std::max<int64_t>(16, (k + 1) / 2) : 0;
+        // curve neighbours per side for the seeding window: k (measured best from k = 8 to
+        // 64 on the LiDAR tile; much narrower windows leave the walk many insertions)
+        a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? sfc::knn_default_window(k) : 0;
         if (k <= 8) SFC_TRY(sfc::launch_knn<8>(t, a, s));
         else if (k <= 16) SFC_TRY(sfc::launch_knn<16>(t, a, s));
         else if (k <= 32) SFC_TRY(sfc::launch_knn<32>(t, a, s));

@@ -307,4 +307,4 @@ def test_autotune_choices_are_valid_and_keep_results():
         assert t["knn_window"] in ((16, 32) if sp["search"] == "knn" and sp["n"] > 0 else (0,))
     _same(sfc.batch_search(pts, tuned, "hilbert"), sfc.batch_search(pts, specs, "hilbert"), specs)
     with pytest.raises(sfc.SFCError):
-        sfc.batch_autotune(pts, specs, "hilbert", window_candidates=(33,))
+        sfc.batch_autotune(pts, specs, "hilbert", window_candidates=(65,))
