@@ -240,7 +240,10 @@ __device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
 // them there.  Per chunk, pass 1 marks the points that beat each lane's current k-th pair
 // and pass 2 lets each lane insert its marked points.
 template <int KMAX>
-__global__ void __launch_bounds__(knn_warps<KMAX>() * 32) k_knn_group(KnnArgs a) {
+// the minimum resident blocks match what shared memory allows for each list size (the
+// register budget never becomes the tighter limit)
+__global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX <= 16 ? 28 : (KMAX <= 32 ? 18 : 10)))
+    k_knn_group(KnnArgs a) {
     constexpr int kWarps = knn_warps<KMAX>();
     // staged points: the seeding window (32 + 2 window - 1 positions) or one leaf chunk
     constexpr int kBuf = KMAX <= 32 ? 96 : 32 + 2 * KMAX;

@@ -118,7 +118,9 @@ __device__ __forceinline__ NodeBox shfl_box(const NodeBox& b, int src) {
 constexpr uint32_t kNoRun = 0xffffffffu;
 
 template <int KERN, bool FILL, bool RUNS>
-__global__ void __launch_bounds__(radius_warps<FILL>() * 32) k_radius_group(RadiusArgs a) {
+// 18 two-warp fill blocks per SM (at most 56 registers) keep 36 warps resident: the fill
+// waits on memory more than the count pass does
+__global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_radius_group(RadiusArgs a) {
     constexpr int kRadiusWarps = radius_warps<FILL>();
     __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
     __shared__ uint32_t stack_w[kRadiusWarps][kStackDepth];  // lanes taking the node whole
