@@ -52,7 +52,9 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 205462272 + 1250616832, "sha256": "7e640b78ee04f964a82bca242292a18ba9c08fe43e59d362f56de870c10a184f"},
+    "knn": {"bytes_per_launch": 204349952 + 1250123520, "sha256": "1e806a41f42ef7abd82fef2987369227876d081c0bb166a45d64efc5154cc7e9"},
+    "radius_fill": {"bytes_per_launch": 3086453760 + 4270319616, "sha256": "078b41b83d7fc03f50dec817dbeab55779469e4a004b49001c5e64b6bb50694a"},
+    "radius_count": {"bytes_per_launch": 322871040 + 920833024, "sha256": "078b41b83d7fc03f50dec817dbeab55779469e4a004b49001c5e64b6bb50694a"},
 }
 
 
@@ -197,8 +199,12 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
 
 
 def source_sha(name: str) -> str:
-    with open(os.path.join(ROOT, "paper_2603_06771_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 of a kernel source together with the shared device header it includes."""
+    h = hashlib.sha256()
+    for part in (name, "sfc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_06771_gb300", "csrc", part), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def load_peaks() -> tuple[float, str]:
