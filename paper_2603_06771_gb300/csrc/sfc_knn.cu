@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
     constexpr int kWarps = knn_warps<KMAX>();
     // staged points: the seeding window (32 + 2 window - 1 positions) or one leaf chunk
     constexpr int kBuf = KMAX <= 32 ? 96 : 32 + 2 * KMAX;
+    static_assert(kBuf >= 64, "the walk keeps a chunk and the centres in the staging buffer");
     __shared__ int4 stack_e[kWarps][kStackDepth];  // first child, start, end, lanes needing it
     __shared__ uint64_t heaps[kWarps][KMAX][32];
     __shared__ float4 pbuf[kWarps][kBuf];
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
     // first output entry of this lane's row
     const int64_t out_base = out0 + static_cast<int64_t>(__float_as_uint(c.w)) * k;
     float4* buf = pbuf[warp];
+    float4* cbuf = buf + 32;  // during the walk: the centres with their current k-th distance
 
     // centre (orders the walk) and bounding box (prunes it) of the group's centres
     const unsigned int act = __ballot_sync(0xffffffffu, active);
@@ -427,17 +429,35 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
             }
             __syncwarp();
         } else {
+            const unsigned int needing = __ballot_sync(0xffffffffu, need);
+            const uint32_t n_need = static_cast<uint32_t>(__popc(needing));
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
-                if (lane < m) buf[lane] = __ldg(&a.pts[base + lane]);
-                __syncwarp();
+                const float4 mine = lane < m ? __ldg(&a.pts[base + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                buf[lane] = mine;
                 // pass 1 compares distances only (<= keeps ties for the exact test of pass 2)
                 const float kd = best.kth_d2();
+                cbuf[lane] = make_float4(c.x, c.y, c.z, kd);
+                __syncwarp();
                 uint32_t cand = 0;
+                if (n_need < m) {
+                    // fewer centres than points: every lane holds a point, the centres come in turn
+                    unsigned int todo = needing;
+                    while (todo) {
+                        const int l = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const float4 cl = cbuf[l];
+                        const bool in = lane < m && sq_dist(__fsub_rn(mine.x, cl.x), __fsub_rn(mine.y, cl.y),
+                                                            __fsub_rn(mine.z, cl.z)) <= cl.w;
+                        const uint32_t b = __ballot_sync(0xffffffffu, in);
+                        if (lane == static_cast<unsigned int>(l)) cand = b;
+                    }
+                } else {
 #pragma unroll 8
-                for (uint32_t t = 0; t < m; ++t) {
-                    const float4 q = buf[t];
-                    if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << t;
+                    for (uint32_t t = 0; t < m; ++t) {
+                        const float4 q = buf[t];
+                        if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << t;
+                    }
                 }
                 // positions this lane already saw in its seeding window
                 const int64_t lo = max(win_lo, static_cast<int64_t>(base));
