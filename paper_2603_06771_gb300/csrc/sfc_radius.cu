@@ -246,16 +246,31 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     if (FILL && a.rec_mode == 2) {
         const uint32_t nrec = a.rec_count[group];
         if (nrec <= static_cast<uint32_t>(a.rec_cap)) {  // else the records overflowed: walk again
+            // three records in flight: while record k is written, record k + 1's ids and
+            // record k + 2's header and masks are loading
+            const int64_t slot0 = group * a.rec_cap;
+            auto head_of = [&](uint32_t k) { return k < nrec ? a.rec_head[slot0 + k] : make_uint2(0u, 0u); };
+            auto mask_of = [&](uint32_t k) { return (k < nrec && active) ? a.rec_masks[(slot0 + k) * 32 + lane] : 0u; };
+            auto ids_of = [&](uint2 hd) {
+                return (!RUNS && !(hd.y & kRangeBit) && lane < hd.y) ? static_cast<int32_t>(a.perm[hd.x + lane]) : 0;
+            };
+            uint2 hd = head_of(0), hd1 = head_of(1);
+            uint32_t mask = mask_of(0), mask1 = mask_of(1);
+            int32_t my_id = ids_of(hd);
             for (uint32_t k = 0; k < nrec; ++k) {
-                const int64_t slot = group * a.rec_cap + k;
-                const uint2 hd = a.rec_head[slot];
-                const uint32_t mask = active ? a.rec_masks[slot * 32 + lane] : 0u;
+                const uint2 hd2 = head_of(k + 2);
+                const uint32_t mask2 = mask_of(k + 2);
+                const int32_t id1 = ids_of(hd1);
                 if (hd.y & kRangeBit) {
                     take_range(__ballot_sync(0xffffffffu, mask != 0), hd.x, hd.y & ~kRangeBit, mask != 0);
                 } else {
-                    const int32_t my_id = (!RUNS && lane < hd.y) ? static_cast<int32_t>(a.perm[hd.x + lane]) : 0;
                     take_hits(mask, my_id, hd.x);
                 }
+                hd = hd1;
+                hd1 = hd2;
+                mask = mask1;
+                mask1 = mask2;
+                my_id = id1;
             }
             finish_runs();
             if (!guard_ok) atomicOr(a.err, kGuardTripped);
