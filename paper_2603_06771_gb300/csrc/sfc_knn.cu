@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
     k_knn_group(KnnArgs a) {
     constexpr int kWarps = knn_warps<KMAX>();
     // staged points: the seeding window (32 + 2 window - 1 positions) or one leaf chunk
-    constexpr int kBuf = KMAX <= 32 ? 96 : 32 + 2 * KMAX;
+    constexpr int kBuf = KMAX <= 16 ? 64 : 32 + 2 * KMAX;
     static_assert(kBuf >= 64, "the walk keeps a chunk and the centres in the staging buffer");
     __shared__ int4 stack_e[kWarps][kStackDepth];  // first child, start, end, lanes needing it
     __shared__ uint64_t heaps[kWarps][KMAX][32];
