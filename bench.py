@@ -52,9 +52,9 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 204349952 + 1250123520, "sha256": "remeasure"},
-    "radius_fill": {"bytes_per_launch": 3086453760 + 4270319616, "sha256": "remeasure"},
-    "radius_count": {"bytes_per_launch": 322871040 + 920833024, "sha256": "remeasure"},
+    "knn": {"bytes_per_launch": 204302592 + 1250119936, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
+    "radius_fill": {"bytes_per_launch": 3074799616 + 4244870400, "sha256": "8462a6ac46b3a35e98de1e03fb45186e469d357b06300214f75f292594b374c1"},
+    "radius_count": {"bytes_per_launch": 322911232 + 920729088, "sha256": "8462a6ac46b3a35e98de1e03fb45186e469d357b06300214f75f292594b374c1"},
 }
 
 
