@@ -58,6 +58,16 @@ NCU_TRAFFIC = {
 }
 
 
+# warp instructions per group of 32 centres of the dominant kernels, from the full ncu set
+# of the 2M-point tile (profiles/search_kernels_full_lidar_tile_2M.md), keyed like the traffic
+NCU_INST_PER_GROUP = {
+    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
+    "radius_count": {"warp_inst": 862614629 / 62500, "sha256": "8462a6ac46b3a35e98de1e03fb45186e469d357b06300214f75f292594b374c1"},
+    "radius_fill": {"warp_inst": 697361326 / 62500, "sha256": "8462a6ac46b3a35e98de1e03fb45186e469d357b06300214f75f292594b374c1"},
+}
+SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -666,6 +676,16 @@ def main(argv=None):
                 "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s", "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_avg_ms}
+        # what bounds these kernels: instruction issue (warp instructions per launch from the
+        # ncu capture, scaled by the launch's groups) against one per sub-partition per cycle
+        ins = NCU_INST_PER_GROUP.get(dom_name)
+        if ins and ins.get("sha256") == source_sha(src) and clk and clk.get("sm_mhz"):
+            issued = ins["warp_inst"] * ((n + 31) // 32) / (dom_avg_ms / 1e3)
+            issue_peak = SMS * SMSP_PER_SM * clk["sm_mhz"] * 1e6
+            roof["issue"] = {"achieved": issued, "peak": issue_peak, "unit": "warp instructions/s",
+                             "frac": issued / issue_peak,
+                             "source": "ncu smsp__inst_executed.sum per group of 32 centres (2M-point tile), "
+                                       "peak = 152 SMs x 4 sub-partitions x median SM clock"}
     kernels = {name: {"launches": c, "total_ms": ms, "share": ms / sum(step_ms)} for name, (c, ms) in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
