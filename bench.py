@@ -250,6 +250,25 @@ def time_oracle(xyz: np.ndarray, cfg: dict, sample: int, seed: int, build_s: flo
     return build_s, radius_s, knn_s
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_step_estimate(n: int, sample: int, build_s: float, radius_s: float, knn_s: float) -> float:
     """Seconds of one full step on the CPU: the build plus the sampled searches scaled to n centres."""
     return build_s + (radius_s + knn_s) * n / sample
@@ -741,10 +760,24 @@ def main(argv=None):
         sample = min(n, 20000)
         b_s, r_s, k_s = time_oracle(xyz, cfg, sample, 7)
         est = cpu_step_estimate(n, sample, b_s, r_s, k_s)
+        # one thread, on a tenth of the sample
+        rows1 = np.sort(np.random.default_rng(8).choice(n, max(1, sample // 10), replace=False))
+        t0 = time.perf_counter()
+        time_oracle.pipe.tree.radius(xyz[rows1], cfg["radius"]["r"], oracle.KERNELS[cfg["radius"]["kernel"]], 1)
+        time_oracle.pipe.tree.knn(xyz[rows1], cfg["knn_k"], 1)
+        one_s = (time.perf_counter() - t0) * n / len(rows1) + b_s
+        # binary32 decisions that binary64 would take the other way (a brute-force scan, so
+        # on 2000 of the sampled centres)
+        rows_b = np.sort(np.random.default_rng(7).choice(n, min(n, 2000), replace=False))
+        boundary = oracle.boundary_disagreements(xyz, xyz[rows_b], cfg["radius"]["r"],
+                                                 oracle.KERNELS[cfg["radius"]["kernel"]])
         cpu = {"value": 2 * n / est, "unit": UNIT, "cores": oracle.num_cpus(), "kind": "oracle",
+               "cpu_model": cpu_model(), "single_thread_value": 2 * n / one_s,
+               "boundary_disagreements": {"centres": len(rows_b), "pairs_decided_differently_in_binary64": boundary},
                "sample": (f"full oracle build of the {n}-point cloud ({b_s:.2f} s, 1 thread) + sphere r=2 "
                           f"({r_s:.3f} s) and kNN k=16 ({k_s:.3f} s) for {sample} seeded centres on "
-                          f"{oracle.num_cpus()} threads, scaled to {n} centres")}
+                          f"{oracle.num_cpus()} threads, scaled to {n} centres; single_thread_value: the "
+                          f"same searches on {len(rows1)} centres on one thread")}
 
     if rank == 0:
         line = {

@@ -124,3 +124,27 @@ def test_knn_sampled_rows(tile, trees, enc, k):
     # every row ascends in (d2, index)
     dd, ii = d2.cpu().numpy(), idx.cpu().numpy()
     assert ((dd[:, 1:] > dd[:, :-1]) | ((dd[:, 1:] == dd[:, :-1]) & (ii[:, 1:] > ii[:, :-1]))).all()
+
+
+def test_every_row_sphere_r2_and_knn16_benchmark_config(tile):
+    """Every row of the benchmark's searches (Hilbert, leaf capacity 64): the oracle answers
+    all 10M centres (its pointer octree, all host cores); neighbour sets are compared row by
+    row after sorting each row by id on the device, kNN lists exactly."""
+    xyz, p = tile["xyz"], tile["p"]
+    t = sfc.octree_build(tile["dev"], "hilbert", leaf_capacity=64)
+    rp, cols = sfc.radius_search(t, None, 2.0, "sphere")
+    orp, ocols = p.tree.radius(xyz, 2.0, oracle.SPHERE)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+
+    def row_sorted(row_ptr: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
+        rows = torch.repeat_interleave(torch.arange(len(row_ptr) - 1, device="cuda"), torch.diff(row_ptr))
+        return torch.sort((rows << 32) | c.to(torch.int64)).values
+
+    want = row_sorted(torch.from_numpy(orp).cuda(), torch.from_numpy(ocols).cuda())
+    assert torch.equal(row_sorted(rp, cols), want)
+    del want, cols, rp
+    idx, d2 = sfc.knn(t, None, 16)
+    oi, od = p.tree.knn(xyz, 16)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint32), od.view(np.uint32))
+    t.free()
