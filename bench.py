@@ -341,6 +341,7 @@ def batch_setup(sfc, torch, n_clouds: int, ncap: int, enc: str):
             redrawn += 1
         sp["nnz"] = nnz
         t.free()
+    batch_setup.xyz = xyz  # the host clouds, for checks
     return specs, pts, views, redrawn
 
 
