@@ -141,3 +141,35 @@ def test_failed_request_does_not_stop_the_server():
     with pytest.raises(sfc.SFCError):
         srv.submit(good, search="radius", r=float("nan"))
     srv.close()
+
+
+def test_real_size_requests_sampled_rows():
+    """Requests of the serving workload's sizes (50k to 20M points, all points or a 1 %
+    subset), sent as a burst: sampled rows of each equal the oracle's brute force."""
+    sizes = (50_000, 2_000_000, 8_000_000, 20_000_000)
+    specs = (dict(search="radius", kernel="sphere", r=2.0), dict(search="knn", k=16),
+             dict(search="radius", kernel="sphere", r=1.0), dict(search="knn", k=32))
+    reqs = []
+    for j, (n, spec) in enumerate(zip(sizes, specs)):
+        xyz = synth.lidar_tile(n, 900 + j)
+        q = None
+        if j % 2 == 1:  # a seeded 1 % subset of the points as centres
+            q = np.ascontiguousarray(xyz[np.sort(synth.Rng(950 + j).integers(0, n // 100, n))])
+        reqs.append((xyz, q, spec))
+    srv = sfc.Server(slots=4)
+    got = _run(srv, reqs, one_at_a_time=False)
+    srv.close()
+    for j, ((xyz, q, spec), g) in enumerate(zip(reqs, got)):
+        centres = xyz if q is None else q
+        rows = np.sort(synth.Rng(970 + j).integers(0, 10, len(centres))).astype(np.int64)
+        if spec["search"] == "radius":
+            orp, ocols = oracle.radius_brute(xyz, centres[rows], spec["r"], KERN[spec["kernel"]])
+            rp = g["row_ptr"].cpu().numpy()
+            for i, row in enumerate(rows):
+                mine = np.sort(g["cols"][rp[row]:rp[row + 1]].cpu().numpy())
+                assert np.array_equal(mine, np.sort(ocols[orp[i]:orp[i + 1]])), (j, int(row))
+        else:
+            oi, od = oracle.knn_brute(xyz, centres[rows], spec["k"])
+            r = torch.as_tensor(rows, device="cuda")
+            assert np.array_equal(g["knn_idx"][r].cpu().numpy(), oi), j
+            assert np.array_equal(g["knn_d2"][r].cpu().numpy().view(np.uint32), od.view(np.uint32)), j
