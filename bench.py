@@ -84,7 +84,7 @@ def parse_args(argv=None):
                     help="neighbour ids (CSR) or runs of sorted positions (range output)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving"], default="lidar_tile_10M")
+    ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving", "sweep"], default="lidar_tile_10M")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -603,9 +603,62 @@ def serve_main(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- sweep
+def sweep_main(args):
+    """Every search of the LiDAR-tile workloads on the resident 10M tile, one JSON line each:
+    4 kernels x r in {0.5, 1, 2, 3} m x 3 orders (count + fill), kNN k in {8, 16, 50} x 3
+    orders, and the build; device time by CUDA events (best of 3, L2 flushed before each)."""
+    import torch
+
+    import paper_2603_06771_gb300 as sfc
+    import synth
+
+    torch.cuda.set_device(0)
+    sfc.build()
+    n = args.points
+    xyz = synth.config_cloud(2) if n == WORKLOAD["points"] else synth.lidar_tile(n, synth.CONFIG_SEED[2])
+    pts = torch.from_numpy(xyz).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def best_ms(fn, reps=3):
+        out = None
+        for rep in range(reps + 1):
+            flush.fill_(rep)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = fn()
+            b.record(stream)
+            b.synchronize()
+            if rep:  # the first is a warm-up
+                out = min(out, a.elapsed_time(b)) if out is not None else a.elapsed_time(b)
+            del res
+        return out
+
+    for enc in ("none", "morton", "hilbert"):
+        build_ms = best_ms(lambda: sfc.octree_build(pts, enc, leaf_capacity=args.leaf_capacity).free())
+        t = sfc.octree_build(pts, enc, leaf_capacity=args.leaf_capacity)
+        print(json.dumps({"sweep": "build", "encoding": enc, "points": n, "ms": build_ms}), flush=True)
+        for kern in ("sphere", "cube", "circle", "square"):
+            for r in (0.5, 1.0, 2.0, 3.0):
+                ms = best_ms(lambda: sfc.radius_search(t, None, r, kern))
+                nnz = int(sfc.radius_count(t, None, r, kern)[1])
+                print(json.dumps({"sweep": "radius", "encoding": enc, "kernel": kern, "r": r, "ms": ms,
+                                  "queries_per_s": n / (ms / 1e3), "neighbours_per_s": nnz / (ms / 1e3),
+                                  "mu": nnz / n}), flush=True)
+        for k in (8, 16, 50):
+            ms = best_ms(lambda: sfc.knn(t, None, k))
+            print(json.dumps({"sweep": "knn", "encoding": enc, "k": k, "ms": ms, "queries_per_s": n / (ms / 1e3)}),
+                  flush=True)
+        t.free()
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "sweep" and args.impl == "ours":
+        return sweep_main(args)
     if args.workload == "batch256" and args.impl == "ours":
         return batch_main(args)
     if args.workload == "serving" and args.impl == "ours":
