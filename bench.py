@@ -84,6 +84,7 @@ def parse_args(argv=None):
                     help="neighbour ids (CSR) or runs of sorted positions (range output)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving", "sweep"], default="lidar_tile_10M")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -192,7 +193,8 @@ def run_step(sfc, pts, cfg):
 
 
 def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
-    """Bytes one launch of ``kernel`` must move at minimum (the per-unit figures of the design doc)."""
+    """Bytes one launch of ``kernel`` must move at minimum: its per-unit algorithmic bytes
+    (points and ids read, row pointers, neighbour ids or kNN pairs written) times the units."""
     table = {
         "radius_fill": 16 * n + 8 * (n + 1) + 4 * nnz,   # points + ids, row pointers, neighbour ids
         "radius_ranges_fill": 16 * n + 8 * (n + 1) + 8 * nnz,  # points, run pointers, runs (nnz = runs)
@@ -411,8 +413,8 @@ def batch_main(args):
 
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks = ClockSampler(local, os.path.join(args.clocks_csv, f"clocks_batch_rank{rank}.csv")
+                          if args.clocks_csv else None)
     clocks.start()
     time.sleep(0.3)
     launches0 = sfc.launch_count()
@@ -574,8 +576,8 @@ def serve_main(args):
               encoding=args.encoding, leaf_capacity=args.leaf_capacity)
     warm = serve_trace(1.0, 20.0, pool_sizes, 7)  # loads the library paths and the memory pool
     serve_run(sfc, torch, warm, pool, big, kw)
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks = ClockSampler(local, os.path.join(args.clocks_csv, f"clocks_serve_rank{rank}.csv")
+                          if args.clocks_csv else None)
     clocks.start()
     launches0 = sfc.launch_count()
     ours = serve_run(sfc, torch, trace, pool, big, kw)
@@ -699,8 +701,8 @@ def main(argv=None):
     torch.cuda.synchronize()
 
     # timed region: K steps, L2 flushed before each, CUDA events around each step
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks = ClockSampler(local, os.path.join(args.clocks_csv, f"clocks_rank{rank}.csv")
+                          if args.clocks_csv else None)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:

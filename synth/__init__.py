@@ -45,7 +45,8 @@ _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
-#: Seed of workload ``k`` (1-based, in the order the workloads are listed in the design doc).
+#: Seed of workload ``k``: 1 uniform cube, 2 LiDAR tile (10M), 3 LiDAR tiles for kNN (10M,
+#: 50M), 4 batch of clouds, 5 serving requests.
 CONFIG_SEED = {k: 0x5EED0000 + k for k in range(1, 6)}
 
 
