@@ -356,14 +356,21 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
                         keep = kernel_holds<KERN>(axis_gap(cb.lo.x, cb.hi.x, glx, ghx),
                                                   axis_gap(cb.lo.y, cb.hi.y, gly, ghy),
                                                   axis_gap(cb.lo.z, cb.hi.z, glz, ghz), r, r2);
+                    // the children for every lane, in the (idle) chunk buffer
+                    chunk[warp][2 * lane] = cb.lo;
+                    chunk[warp][2 * lane + 1] = cb.hi;
+                    chunk[warp][16 + lane] = make_float4(__int_as_float(cc), 0.f, 0.f, 0.f);
                 }
                 unsigned int kept = __ballot_sync(0xffffffffu, keep);
+                __syncwarp();
                 // push the last child first so that the first child is popped first
                 while (kept) {
                     const int ci = 31 - __clz(kept);
                     kept &= ~(1u << ci);
-                    const NodeBox b = shfl_box(cb, ci);
-                    const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
+                    NodeBox b;
+                    b.lo = chunk[warp][2 * ci];
+                    b.hi = chunk[warp][2 * ci + 1];
+                    const int32_t bc = __float_as_int(chunk[warp][16 + ci].x);
                     // a lane that found the parent disjoint or took it whole has nothing here
                     const int cls = my_partial ? classify_box<KERN>(b, c.x, c.y, c.z, r, r2, prune) : 0;
                     const unsigned int cp = __ballot_sync(0xffffffffu, cls == 1);
