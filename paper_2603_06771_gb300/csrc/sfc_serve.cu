@@ -237,12 +237,32 @@ void worker(sfc_server_s* S, int slot) {
         }
         std::shared_ptr<Pass> pass;
         // alone (nothing queued to merge with, or query centres given): the single-cloud path
-        const sfc_status st = group.size() == 1 ? run_single(S, *group[0], s) : run_merged(S, group, s, pass);
-        if (st != SFC_OK) cudaStreamSynchronize(s);
+        std::vector<sfc_status> status(group.size(), SFC_OK);
+        if (group.size() == 1) {
+            status[0] = run_single(S, *group[0], s);
+        } else if (run_merged(S, group, s, pass) != SFC_OK) {
+            // one request of the merged pass failed (a non-finite cloud, say): answer each
+            // alone, so that only the failing one reports the failure
+            cudaStreamSynchronize(s);
+            for (Request* q : group) {
+                q->pass.reset();
+                q->cloud = -1;
+                q->batched_with = 1;
+                q->csr = sfc_csr{};
+            }
+            pass.reset();
+            for (size_t i = 0; i < group.size(); ++i) {
+                status[i] = run_single(S, *group[i], s);
+                if (status[i] != SFC_OK) cudaStreamSynchronize(s);
+            }
+        }
+        if (group.size() == 1 && status[0] != SFC_OK) cudaStreamSynchronize(s);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             const Clock::time_point now = Clock::now();
-            for (Request* q : group) {
+            for (size_t i = 0; i < group.size(); ++i) {
+                Request* q = group[i];
+                const sfc_status st = status[i];
                 q->done = now;
                 q->status = st;
                 q->finished = true;

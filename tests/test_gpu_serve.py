@@ -122,6 +122,34 @@ def test_budget_admits_one_at_a_time():
     srv.close()
 
 
+def test_failed_request_in_a_merged_pass_fails_alone():
+    """A non-finite cloud merged with good ones: the merged pass fails, its requests are
+    answered one by one, and only the bad one reports the failure."""
+    srv = sfc.Server(slots=1, max_batch=8, batch_points=1_000_000)
+    blocker = srv.submit(synth.lidar_tile(4_000_000, 77), search="knn", k=32)  # holds the only slot
+    bad = synth.uniform_cube(3000, 78)
+    bad[5, 0] = np.nan
+    goods = [synth.uniform_cube(3000, 79 + j) for j in range(3)]
+    ids = [srv.submit(goods[0], search="knn", k=8), srv.submit(bad, search="knn", k=8),
+           srv.submit(goods[1], search="radius", kernel="sphere", r=0.1),
+           srv.submit(goods[2], search="knn", k=4)]
+    assert srv.wait(blocker) == 0
+    assert [srv.wait(i) for i in ids] == [0, 7, 0, 0]
+    for i, (g, spec) in zip((ids[0], ids[2], ids[3]), zip((goods[0], goods[1], goods[2]),
+                                                         (dict(k=8), dict(r=0.1), dict(k=4)))):
+        res = srv.result(i)
+        assert res["batched_with"] == 1 and res["rows"] == 3000
+        if "k" in spec:
+            oi, _ = oracle.knn_brute(g, g, spec["k"])
+            assert np.array_equal(res["knn_idx"].cpu().numpy(), oi)
+        else:
+            orp, _ = oracle.radius_brute(g, g, spec["r"], oracle.SPHERE)
+            assert np.array_equal(res["row_ptr"].cpu().numpy(), orp)
+    for i in [blocker] + ids:
+        srv.release(i)
+    srv.close()
+
+
 def test_failed_request_does_not_stop_the_server():
     srv = sfc.Server(slots=2)
     bad = synth.uniform_cube(1000, 5)
