@@ -398,6 +398,24 @@ sfc_status server_stats(sfc_server s, sfc_server_stats* out);
 /* Finish the queued requests, stop the workers and free everything. */
 sfc_status server_destroy(sfc_server s);
 
+/* ---- device memory ---------------------------------------------------------------- */
+
+/* A caller's device allocator (e.g. a framework's caching allocator): alloc returns
+ * `bytes` of device memory usable in stream order on cuda_stream, or NULL; free releases
+ * it in stream order.  Both may be called from any host thread (the server's workers). */
+typedef void* (*sfc_alloc_fn)(size_t bytes, void* ctx, void* cuda_stream);
+typedef void (*sfc_free_fn)(void* p, void* ctx, void* cuda_stream);
+
+/* Route every device allocation of the library (octrees, search outputs it allocates,
+ * scratch) through alloc / free; both NULL restores the stream-ordered allocator.  The
+ * temporaries recorded into a batch plan's graph always use the stream-ordered allocator.
+ * SFC_ERR_INVALID when exactly one of the two is NULL, or while library allocations are
+ * alive (every allocation is freed by the allocator that made it). */
+sfc_status sfc_set_allocator(sfc_alloc_fn alloc, sfc_free_fn free_fn, void* ctx);
+
+/* Library device allocations alive now (octrees, outputs, plans, records). */
+int64_t sfc_live_allocations(void);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------ */
 
 /* Copy the sorted codes (n), the permutation sorted position -> original index (n), the

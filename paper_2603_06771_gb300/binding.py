@@ -16,7 +16,7 @@ from .build import LIB
 
 __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
-    "radius_search_ranges", "knn_locality", "choose_encoding",
+    "radius_search_ranges", "knn_locality", "choose_encoding", "use_torch_allocator", "live_allocations",
     "Batch", "batch_search", "BatchPlan", "batch_autotune", "Server",
     "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
 ]
@@ -80,6 +80,8 @@ _SIGNATURES = {
     "knn_locality": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     "choose_encoding": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sfc_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sfc_live_allocations": (C.c_int64, []),
     "batch_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "batch_cloud_result": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
@@ -679,3 +681,34 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- device memory
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+def _torch_alloc(nbytes, ctx, stream):
+    s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+    return torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(), stream=s)
+
+
+def _torch_free(ptr, ctx, stream):
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+_HOOKS = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))  # kept alive for the library
+
+
+def use_torch_allocator(on: bool = True):
+    """``sfc_set_allocator`` with torch's caching allocator (``on``) or back to the
+    stream-ordered allocator; only while no library allocation is alive."""
+    if on:
+        _check(lib().sfc_set_allocator(C.cast(_HOOKS[0], C.c_void_p), C.cast(_HOOKS[1], C.c_void_p), None),
+               "sfc_set_allocator")
+    else:
+        _check(lib().sfc_set_allocator(None, None, None), "sfc_set_allocator")
+
+
+def live_allocations() -> int:
+    return int(lib().sfc_live_allocations())

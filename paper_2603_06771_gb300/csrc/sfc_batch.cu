@@ -1013,7 +1013,7 @@ static sfc_status capture_plan(sfc_batch_plan_s* P) {
     SFC_CUDA(cudaStreamBeginCapture(P->cs, cudaStreamCaptureModeThreadLocal));
     sfc_status st = SFC_OK;
     {
-        Scratch tmp(P->cs);  // temporaries of one run (sort and scan work arrays): graph allocations
+        Scratch tmp(P->cs, true);  // temporaries of one run (sort and scan work arrays): graph allocations
         const cudaStream_t s = P->cs;
         BatchBuffers& b = P->b;
         st = enqueue_order(P->T, b, P->xyz, P->enc, s, tmp);

@@ -128,17 +128,23 @@ sfc_status launch_end(const char* name, cudaStream_t s);
 bool is_device_ptr(const void* p);
 sfc_status ensure_pool(int device);
 
-// Stream-ordered scratch allocations, released (in stream order) when the guard dies.
+// Every device allocation of the library: through the caller's allocator when one is set
+// (sfc_set_allocator), else the stream-ordered allocator; `native` always takes the
+// latter (allocations recorded into a CUDA graph).  A free must use the same `native`.
+cudaError_t raw_alloc(void** p, size_t bytes, cudaStream_t s, bool native = false);
+void raw_free(void* p, cudaStream_t s, bool native = false);
+
+// Scratch allocations, released (in stream order) when the guard dies.
 class Scratch {
   public:
-    explicit Scratch(cudaStream_t s) : s_(s) {}
+    explicit Scratch(cudaStream_t s, bool native = false) : s_(s), native_(native) {}
     ~Scratch();
     template <typename T>
     sfc_status alloc(T** p, size_t count) {
         void* v = nullptr;
-        cudaError_t e = cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s_);
+        cudaError_t e = raw_alloc(&v, (count ? count : 1) * sizeof(T), s_, native_);
         if (e != cudaSuccess) {
-            record_cuda_error(e, "cudaMallocAsync");
+            record_cuda_error(e, "device allocation");
             *p = nullptr;
             return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
         }
@@ -150,7 +156,7 @@ class Scratch {
     template <typename T>
     bool try_alloc(T** p, size_t count) {
         void* v = nullptr;
-        if (cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s_) != cudaSuccess) {
+        if (raw_alloc(&v, (count ? count : 1) * sizeof(T), s_, native_) != cudaSuccess) {
             cudaGetLastError();
             *p = nullptr;
             return false;
@@ -165,15 +171,16 @@ class Scratch {
 
   private:
     cudaStream_t s_;
+    bool native_;
     std::vector<void*> ptrs_;
 };
 
 template <typename T>
 sfc_status dev_alloc(T** p, size_t count, cudaStream_t s) {
     void* v = nullptr;
-    cudaError_t e = cudaMallocAsync(&v, (count ? count : 1) * sizeof(T), s);
+    cudaError_t e = raw_alloc(&v, (count ? count : 1) * sizeof(T), s);
     if (e != cudaSuccess) {
-        record_cuda_error(e, "cudaMallocAsync");
+        record_cuda_error(e, "device allocation");
         *p = nullptr;
         return e == cudaErrorMemoryAllocation ? SFC_ERR_OOM : SFC_ERR_CUDA;
     }

@@ -597,9 +597,9 @@ static void setup_records(Octree* t, int64_t rows, float r, int kern, cudaStream
     RadiusRecords& rec = t->records;
     const int64_t groups = (rows + 31) / 32;
     const int64_t slots = groups * kRecordCap;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&rec.masks), sizeof(uint32_t) * 32 * slots, s) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&rec.head), sizeof(uint2) * slots, s) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&rec.count), sizeof(uint32_t) * groups, s) != cudaSuccess) {
+    if (raw_alloc(reinterpret_cast<void**>(&rec.masks), sizeof(uint32_t) * 32 * slots, s) != cudaSuccess ||
+        raw_alloc(reinterpret_cast<void**>(&rec.head), sizeof(uint2) * slots, s) != cudaSuccess ||
+        raw_alloc(reinterpret_cast<void**>(&rec.count), sizeof(uint32_t) * groups, s) != cudaSuccess) {
         cudaGetLastError();
         release_records(t, s);
         return;

@@ -94,8 +94,49 @@ sfc_status ensure_pool(int device) {
     return SFC_OK;
 }
 
+// the caller's allocator, and how many library allocations are alive (it may change only
+// while none is)
+static std::mutex g_alloc_mu;
+static sfc_alloc_fn g_alloc = nullptr;
+static sfc_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::atomic<int64_t> g_live{0};
+
+cudaError_t raw_alloc(void** p, size_t bytes, cudaStream_t s, bool native) {
+    sfc_alloc_fn fn = nullptr;
+    void* ctx = nullptr;
+    if (!native) {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        fn = g_alloc;
+        ctx = g_alloc_ctx;
+    }
+    cudaError_t e = cudaSuccess;
+    if (fn) {
+        *p = fn(bytes, ctx, s);
+        if (!*p) e = cudaErrorMemoryAllocation;
+    } else {
+        e = cudaMallocAsync(p, bytes, s);
+    }
+    if (e == cudaSuccess) g_live.fetch_add(1);
+    return e;
+}
+
+void raw_free(void* p, cudaStream_t s, bool native) {
+    if (!p) return;
+    sfc_free_fn fn = nullptr;
+    void* ctx = nullptr;
+    if (!native) {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        fn = g_free;
+        ctx = g_alloc_ctx;
+    }
+    if (fn) fn(p, ctx, s);
+    else cudaFreeAsync(p, s);
+    g_live.fetch_sub(1);
+}
+
 Scratch::~Scratch() {
-    for (void* p : ptrs_) cudaFreeAsync(p, s_);
+    for (void* p : ptrs_) raw_free(p, s_, native_);
 }
 
 void Scratch::release(const void* p) {
@@ -107,9 +148,7 @@ void Scratch::release(const void* p) {
     ptrs_.swap(keep);
 }
 
-void dev_free(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
-}
+void dev_free(void* p, cudaStream_t s) { raw_free(p, s); }
 
 // ---------------------------------------------------------------------------------
 // exclusive scan: tiles of kScanTile elements; per-tile sums, a single-block scan of
@@ -407,6 +446,18 @@ const char* sfc_status_string(sfc_status s) {
 const char* sfc_last_error(void) { return sfc::t_last_error; }
 
 uint64_t sfc_launch_count(void) { return sfc::g_launches.load(); }
+
+sfc_status sfc_set_allocator(sfc_alloc_fn alloc, sfc_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SFC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sfc::g_alloc_mu);
+    if (sfc::g_live.load() != 0) return SFC_ERR_INVALID;
+    sfc::g_alloc = alloc;
+    sfc::g_free = free_fn;
+    sfc::g_alloc_ctx = ctx;
+    return SFC_OK;
+}
+
+int64_t sfc_live_allocations(void) { return sfc::g_live.load(); }
 
 sfc_status sfc_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> g(sfc::g_prof_mu);
