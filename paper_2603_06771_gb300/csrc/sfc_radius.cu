@@ -97,16 +97,6 @@ __device__ __forceinline__ float axis_gap(float lo, float hi, float glo, float g
     return fmaxf(fmaxf(__fsub_rn(lo, ghi), __fsub_rn(glo, hi)), 0.0f);
 }
 
-// Broadcast lane src's node box to the warp.
-__device__ __forceinline__ NodeBox shfl_box(const NodeBox& b, int src) {
-    NodeBox o;
-    o.lo = make_float4(__shfl_sync(0xffffffffu, b.lo.x, src), __shfl_sync(0xffffffffu, b.lo.y, src),
-                       __shfl_sync(0xffffffffu, b.lo.z, src), __shfl_sync(0xffffffffu, b.lo.w, src));
-    o.hi = make_float4(__shfl_sync(0xffffffffu, b.hi.x, src), __shfl_sync(0xffffffffu, b.hi.y, src),
-                       __shfl_sync(0xffffffffu, b.hi.z, src), __shfl_sync(0xffffffffu, b.hi.w, src));
-    return o;
-}
-
 // The walk keeps, per pushed node, what its parent's expansion learnt: its first child,
 // its point range and which lanes find it undecided or wholly inside their kernel, so a
 // pop reads shared memory only.  An expansion loads the eight children once (lanes 0-7),
