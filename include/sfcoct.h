@@ -121,10 +121,12 @@ sfc_status octree_info(sfc_octree h, sfc_octree_info* info);
  *                original order (then n_queries must be 0 or the number of points).
  *   r            radius (for CUBE / SQUARE the half side); r <= 0 gives empty rows, a
  *                NaN r gives SFC_ERR_INVALID.
- *   out          receives a CSR whose two arrays the library allocates with
- *                cudaMallocAsync on cuda_stream; release it with sfc_csr_free.
+ *   out          receives a CSR whose two arrays the library allocates in stream order
+ *                on cuda_stream (its allocator: see sfc_set_allocator); release it with
+ *                sfc_csr_free.
  * Row q lists every tree point p with kernel(p, centre q, r) true, the centre itself
- * included when it is a tree point.  Synchronises cuda_stream once (to read nnz). */
+ * included when it is a tree point.  Synchronises cuda_stream (to read nnz, then the
+ * device guard word). */
 sfc_status radius_search(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
                          void* cuda_stream, sfc_csr* out);
 
