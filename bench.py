@@ -53,8 +53,8 @@ L2_FLUSH_BYTES = 512 << 20
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
     "knn": {"bytes_per_launch": 204302592 + 1250119936, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
-    "radius_fill": {"bytes_per_launch": 3074799616 + 4244870400, "sha256": "remeasure"},
-    "radius_count": {"bytes_per_launch": 322911232 + 920729088, "sha256": "remeasure"},
+    "radius_fill": {"bytes_per_launch": 3077275648 + 4252898304, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
+    "radius_count": {"bytes_per_launch": 325291776 + 925327360, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
 }
 
 
@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
 # of the 2M-point tile (profiles/search_kernels_full_lidar_tile_2M.md), keyed like the traffic
 NCU_INST_PER_GROUP = {
     "knn": {"warp_inst": 1633391437 / 62500, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
-    "radius_count": {"warp_inst": 862614629 / 62500, "sha256": "remeasure"},
-    "radius_fill": {"warp_inst": 697361326 / 62500, "sha256": "remeasure"},
+    "radius_count": {"warp_inst": 839805701 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
+    "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 
