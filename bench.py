@@ -52,7 +52,7 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 204302592 + 1250119936, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
+    "knn": {"bytes_per_launch": 203560704 + 1250418176, "sha256": "e13aec15d818d2dd7dc7cc9baffb40afead4f89cb0ff07c1073f6ebb10566f7f"},
     "radius_fill": {"bytes_per_launch": 3077275648 + 4252898304, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
     "radius_count": {"bytes_per_launch": 325291776 + 925327360, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
 }
@@ -61,7 +61,7 @@ NCU_TRAFFIC = {
 # warp instructions per group of 32 centres of the dominant kernels, from the full ncu set
 # of the 2M-point tile (profiles/search_kernels_full_lidar_tile_2M.md), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "e3d00f46113451e53ac176b1a4a44d34872f24205b59ef02b828369ff1c9012d"},
+    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "e13aec15d818d2dd7dc7cc9baffb40afead4f89cb0ff07c1073f6ebb10566f7f"},
     "radius_count": {"warp_inst": 839805701 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
     "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
 }
