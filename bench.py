@@ -66,6 +66,10 @@ NCU_INST_PER_GROUP = {
     "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
+FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
+# binary32 operations of one centre-point test (subtractions, products, sums or maxima, and
+# the comparison): the secondary, ALU side of the roofline
+FP32_OPS_PER_TEST = {"sphere": 9, "circle": 6, "cube": 6, "square": 4, "knn": 9}
 
 
 def parse_args(argv=None):
@@ -92,6 +96,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-big", action="store_true", help="serving: leave out the 200M-point cloud")
     ap.add_argument("--clouds", type=int, default=256, help="batch256: number of clouds (testing)")
     ap.add_argument("--no-tune", action="store_true", help="batch256: one leaf capacity for every cloud")
+    ap.add_argument("--sweep-oracle-sample", type=int, default=20000,
+                    help="sweep: seeded centres per oracle search (scaled to all centres)")
     return ap.parse_args(argv)
 
 
@@ -208,6 +214,28 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
         "bbox": 12 * n,
     }
     return table.get(kernel)
+
+
+def search_counters(sfc, fn) -> dict:
+    """The library's work counters of the searches ``fn`` runs (instrumented kernels, never
+    timed)."""
+    with sfc.search_stats() as st:
+        fn()
+    return st
+
+
+def alu_side(counters: dict, kind: str, launch_ms: float, sm_mhz: float | None) -> dict:
+    """Candidate tests per second of one launch and their binary32 operations against the
+    FP32 lanes' peak at the sampled SM clock (152 SMs x 128 lanes x clock)."""
+    ops = FP32_OPS_PER_TEST[kind]
+    per_s = counters["point_tests"] / (launch_ms / 1e3)
+    out = {"point_tests": counters["point_tests"], "needed_tests": counters["needed_tests"],
+           "tests_per_s": per_s, "needed_tests_per_s": counters["needed_tests"] / (launch_ms / 1e3),
+           "fp32_ops_per_test": ops, "counters": counters}
+    if sm_mhz:
+        peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6
+        out.update(fp32_ops_per_s=per_s * ops, fp32_peak=peak, fp32_frac=per_s * ops / peak)
+    return out
 
 
 def source_sha(name: str) -> str:
@@ -609,7 +637,11 @@ def serve_main(args):
 def sweep_main(args):
     """Every search of the LiDAR-tile workloads on the resident 10M tile, one JSON line each:
     4 kernels x r in {0.5, 1, 2, 3} m x 3 orders (count + fill), kNN k in {8, 16, 50} x 3
-    orders, and the build; device time by CUDA events (best of 3, L2 flushed before each)."""
+    orders, and the build; device time by CUDA events (best of 3, L2 flushed before each),
+    queries/s, neighbours/s, the fraction of the HBM roofline (algorithmic bytes of the call
+    / time / measured copy bandwidth) and the candidate tests per second with their share of
+    the FP32 lanes.  Then the oracle's searches of every combination on a seeded sample of
+    centres on the host cores, scaled to all centres (unless --no-cpu-baseline)."""
     import torch
 
     import paper_2603_06771_gb300 as sfc
@@ -622,6 +654,9 @@ def sweep_main(args):
     pts = torch.from_numpy(xyz).cuda()
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    peak, peak_kind = load_peaks()
+    clocks = ClockSampler(0, os.path.join(args.clocks_csv, "clocks_sweep.csv") if args.clocks_csv else None)
+    clocks.start()
 
     def best_ms(fn, reps=3):
         out = None
@@ -637,22 +672,69 @@ def sweep_main(args):
             del res
         return out
 
+    lines = []
     for enc in ("none", "morton", "hilbert"):
         build_ms = best_ms(lambda: sfc.octree_build(pts, enc, leaf_capacity=args.leaf_capacity).free())
         t = sfc.octree_build(pts, enc, leaf_capacity=args.leaf_capacity)
-        print(json.dumps({"sweep": "build", "encoding": enc, "points": n, "ms": build_ms}), flush=True)
+        lines.append({"sweep": "build", "encoding": enc, "points": n, "ms": build_ms})
+        print(json.dumps(lines[-1]), flush=True)
         for kern in ("sphere", "cube", "circle", "square"):
             for r in (0.5, 1.0, 2.0, 3.0):
                 ms = best_ms(lambda: sfc.radius_search(t, None, r, kern))
                 nnz = int(sfc.radius_count(t, None, r, kern)[1])
-                print(json.dumps({"sweep": "radius", "encoding": enc, "kernel": kern, "r": r, "ms": ms,
-                                  "queries_per_s": n / (ms / 1e3), "neighbours_per_s": nnz / (ms / 1e3),
-                                  "mu": nnz / n}), flush=True)
+                cnt = search_counters(sfc, lambda: sfc.radius_count(t, None, r, kern))
+                alg = 16 * n + 8 * (n + 1) + 4 * nnz  # points + ids, row pointers, neighbour ids
+                lines.append({"sweep": "radius", "encoding": enc, "kernel": kern, "r": r, "ms": ms,
+                              "queries_per_s": n / (ms / 1e3), "neighbours_per_s": nnz / (ms / 1e3),
+                              "mu": nnz / n, "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
+                              "tests_per_s": cnt["point_tests"] / (ms / 1e3), "counters": cnt,
+                              "fp32_ops_per_test": FP32_OPS_PER_TEST[kern]})
+                print(json.dumps(lines[-1]), flush=True)
         for k in (8, 16, 50):
             ms = best_ms(lambda: sfc.knn(t, None, k))
-            print(json.dumps({"sweep": "knn", "encoding": enc, "k": k, "ms": ms, "queries_per_s": n / (ms / 1e3)}),
-                  flush=True)
+            cnt = search_counters(sfc, lambda: sfc.knn(t, None, k))
+            alg = 16 * n + 8 * n * k  # points + ids, k (id, d2) pairs per centre
+            lines.append({"sweep": "knn", "encoding": enc, "k": k, "ms": ms, "queries_per_s": n / (ms / 1e3),
+                          "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
+                          "tests_per_s": cnt["point_tests"] / (ms / 1e3), "counters": cnt,
+                          "fp32_ops_per_test": FP32_OPS_PER_TEST["knn"]})
+            print(json.dumps(lines[-1]), flush=True)
         t.free()
+    clk = clocks.stop()
+    sm_mhz = clk.get("sm_mhz") if clk else None
+    fp32_peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 if sm_mhz else None
+    print(json.dumps({"sweep": "peaks", "hbm_gbs": peak, "hbm_peak_source": peak_kind, "clocks": clk,
+                      "fp32_peak_ops_per_s": fp32_peak,
+                      "fp32_frac_of": "tests_per_s x fp32_ops_per_test / fp32_peak_ops_per_s"}), flush=True)
+
+    if args.no_cpu_baseline:
+        return 0
+    # the oracle: one pointer octree (its searches do not depend on the curve), every
+    # combination on the same seeded centres, all host threads, scaled to n centres
+    import oracle
+
+    t0 = time.perf_counter()
+    tree = oracle.PointerOctree(xyz, args.leaf_capacity)
+    build_s = time.perf_counter() - t0
+    sample = min(n, args.sweep_oracle_sample)
+    q = xyz[np.sort(np.random.default_rng(11).choice(n, sample, replace=False))]
+    cores = oracle.num_cpus()
+    for kern in ("sphere", "cube", "circle", "square"):
+        for r in (0.5, 1.0, 2.0, 3.0):
+            t0 = time.perf_counter()
+            tree.radius(q, r, oracle.KERNELS[kern])
+            sec = time.perf_counter() - t0
+            print(json.dumps({"sweep": "oracle_radius", "kernel": kern, "r": r, "centres": sample, "s": sec,
+                              "queries_per_s": sample / sec, "cores": cores, "extrapolated": sample < n}),
+                  flush=True)
+    for k in (8, 16, 50):
+        t0 = time.perf_counter()
+        tree.knn(q, k)
+        sec = time.perf_counter() - t0
+        print(json.dumps({"sweep": "oracle_knn", "k": k, "centres": sample, "s": sec, "queries_per_s": sample / sec,
+                          "cores": cores, "extrapolated": sample < n}), flush=True)
+    print(json.dumps({"sweep": "oracle_build", "points": n, "s": build_s, "threads": 1, "cpu_model": cpu_model()}),
+          flush=True)
     return 0
 
 
@@ -764,6 +846,25 @@ def main(argv=None):
     kernels = {name: {"launches": c, "total_ms": ms, "share": ms / sum(step_ms)} for name, (c, ms) in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    # candidate tests of the two search kernels (instrumented copies, run once, untimed)
+    tests = {}
+    t = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
+    sm_mhz = clk.get("sm_mhz") if clk else None
+    if cfg["radius"].get("output") != "ranges" and "radius_count" in prof:
+        c = search_counters(sfc, lambda: sfc.radius_count(t, None, cfg["radius"]["r"], cfg["radius"]["kernel"]))
+        tests["radius_count"] = alu_side(c, cfg["radius"]["kernel"], prof["radius_count"][1] /
+                                         prof["radius_count"][0], sm_mhz)
+    if "knn" in prof:
+        c = search_counters(sfc, lambda: sfc.knn(t, None, k))
+        tests["knn"] = alu_side(c, "knn", prof["knn"][1] / prof["knn"][0], sm_mhz)
+    t.free()
+    if roof is not None and dom_name in tests and "fp32_frac" in tests[dom_name]:
+        a = tests[dom_name]
+        roof["alu"] = {"achieved": a["fp32_ops_per_s"], "peak": a["fp32_peak"], "unit": "FP32 op/s",
+                       "frac": a["fp32_frac"], "tests_per_s": a["tests_per_s"],
+                       "source": "library work counters (point tests executed per launch) x binary32 operations "
+                                 "per test; peak = 152 SMs x 128 FP32 lanes x median SM clock"}
+
     # end to end through the public API: pinned host points in, every result back to pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -844,7 +945,7 @@ def main(argv=None):
                            parallelism="replicas" if world > 1 else "single GPU"),
             "nnz": nnz, "mu": nnz / n, "neighbours_per_s": nnz * args.steps * world / (total_ms / 1e3),
             "gpu_launches": launches, "wall_s": wall_s, "roofline": roof, "kernels": kernels,
-            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "candidate_tests": tests, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

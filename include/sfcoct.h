@@ -454,6 +454,35 @@ sfc_status sfc_profile_enable(int32_t on);
  * total_ms[i]. */
 int32_t sfc_profile_read(char* names, int64_t* launches, double* total_ms, int32_t cap);
 
+/* Work counters of the search walks (the candidate tests of sections 3.2-3.3 and 5.1, for
+ * the ALU side of a roofline).  Summed over every radius count pass (CSR output) and
+ * every kNN search on octree_build handles launched while counting is on, from any
+ * thread (the request server's requests that run alone included); the batched searches
+ * and the range output are not counted.  "Executed" counts every lane
+ * of a warp that runs an evaluation, "needed" only the lanes whose own centre's walk
+ * reaches the leaf (what a walk per centre would test). */
+typedef struct {
+    int64_t walks;         /* warp groups of 32 centres, or walks of one centre (SFC_ENC_NONE) */
+    int64_t expansions;    /* internal nodes whose children were examined */
+    int64_t box_tests;     /* centre-box evaluations executed (one per lane and child examined) */
+    int64_t leaves;        /* leaves whose points were read */
+    int64_t point_tests;   /* centre-point kernel or distance evaluations executed, including
+                              the kNN seeding window along the curve */
+    int64_t needed_tests;  /* of those, by lanes whose own walk reaches the leaf */
+    int64_t passed;        /* radius: hits; kNN: points marked as candidates */
+    int64_t whole;         /* radius: neighbours taken inside whole nodes (step 1a, no test) */
+    int64_t inserts;       /* kNN: insertions into a centre's list of k best */
+} sfc_search_stats;
+
+/* on != 0 zeroes the counters (synchronising the device) and makes the searches launch an
+ * instrumented copy of their kernels: the same results, more registers and instructions,
+ * so never time a search while counting.  0 stops counting.  SFC_ERR_CUDA if the
+ * counters cannot be allocated. */
+sfc_status sfc_stats_enable(int32_t on);
+/* Synchronises the device and copies the counters into *out (all zero if counting was
+ * never enabled).  SFC_ERR_INVALID for out == NULL. */
+sfc_status sfc_stats_read(sfc_search_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

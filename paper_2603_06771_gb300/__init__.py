@@ -9,10 +9,12 @@ arriving over time with ``Server``.
 from .binding import (ENCODINGS, KERNELS, Batch, BatchPlan, Octree, Server, SFCError, batch_autotune,
                       batch_search, choose_encoding, encode_cells, knn, knn_locality, launch_count, library_path,
                       live_allocations, octree_build, profile_enable, profile_read, radius_count, radius_fill,
-                      radius_search, radius_search_csr, radius_search_ranges, use_torch_allocator)
+                      radius_search, radius_search_csr, radius_search_ranges, search_stats, stats_enable, stats_read,
+                      use_torch_allocator)
 from .build import build
 
 __all__ = ["ENCODINGS", "KERNELS", "Batch", "BatchPlan", "Octree", "Server", "SFCError", "batch_autotune",
            "batch_search", "build", "choose_encoding", "encode_cells", "knn", "knn_locality", "launch_count",
            "library_path", "live_allocations", "octree_build", "profile_enable", "profile_read", "radius_count",
-           "radius_fill", "radius_search", "radius_search_csr", "radius_search_ranges", "use_torch_allocator"]
+           "radius_fill", "radius_search", "radius_search_csr", "radius_search_ranges", "search_stats", "stats_enable",
+           "stats_read", "use_torch_allocator"]

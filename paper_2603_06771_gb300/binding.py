@@ -6,6 +6,7 @@ built, or a call fails, a Python exception is raised; there is no CPU fallback.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import threading
@@ -18,7 +19,8 @@ __all__ = [
     "SFCError", "Octree", "octree_build", "radius_search", "radius_count", "radius_fill", "radius_search_csr",
     "radius_search_ranges", "knn_locality", "choose_encoding", "use_torch_allocator", "live_allocations",
     "Batch", "batch_search", "BatchPlan", "batch_autotune", "Server",
-    "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "library_path", "ENCODINGS", "KERNELS",
+    "knn", "encode_cells", "launch_count", "profile_enable", "profile_read", "stats_enable", "stats_read",
+    "search_stats", "library_path", "ENCODINGS", "KERNELS",
 ]
 
 ENCODINGS = {"none": 0, "morton": 1, "hilbert": 2}
@@ -108,6 +110,8 @@ _SIGNATURES = {
     "sfc_launch_count": (C.c_uint64, []),
     "sfc_profile_enable": (C.c_int, [C.c_int32]),
     "sfc_profile_read": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "sfc_stats_enable": (C.c_int, [C.c_int32]),
+    "sfc_stats_read": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -404,6 +408,39 @@ def profile_read() -> dict:
         name = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         out[name] = (int(launches[i]), float(ms[i]))
     return out
+
+
+class _SearchStats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in ("walks", "expansions", "box_tests", "leaves", "point_tests",
+                                               "needed_tests", "passed", "whole", "inserts")]
+
+
+def stats_enable(on: bool = True):
+    """Zero the search work counters and count (``on``), or stop counting.  While counting,
+    the searches run instrumented kernels: same results, slower; do not time them."""
+    _check(lib().sfc_stats_enable(1 if on else 0), "sfc_stats_enable")
+
+
+def stats_read() -> dict:
+    """The work counters summed since ``stats_enable`` (``sfc_search_stats``), as a dict."""
+    st = _SearchStats()
+    _check(lib().sfc_stats_read(C.byref(st)), "sfc_stats_read")
+    return {name: int(getattr(st, name)) for name, _ in _SearchStats._fields_}
+
+
+@contextlib.contextmanager
+def search_stats():
+    """``with search_stats() as st: ...`` counts the searches of the block; ``st`` is filled
+    with ``stats_read()`` when the block ends."""
+    out: dict = {}
+    stats_enable(True)
+    try:
+        yield out
+    finally:
+        try:
+            out.update(stats_read())
+        finally:
+            stats_enable(False)
 
 
 # ----------------------------------------------------------------------------- batched path

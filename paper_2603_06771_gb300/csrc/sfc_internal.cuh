@@ -128,6 +128,11 @@ sfc_status launch_end(const char* name, cudaStream_t s);
 bool is_device_ptr(const void* p);
 sfc_status ensure_pool(int device);
 
+// Work counters of the search kernels (sfc_stats_enable): the counters' device array while
+// counting is on, else nullptr.  The searches launch an instrumented copy of their kernel
+// when it is not null.
+unsigned long long* stats_counters();
+
 // Every device allocation of the library: through the caller's allocator when one is set
 // (sfc_set_allocator), else the stream-ordered allocator; `native` always takes the
 // latter (allocations recorded into a CUDA graph).  A free must use the same `native`.
@@ -308,6 +313,43 @@ __device__ __forceinline__ bool kernel_holds(float dx, float dy, float dz, float
         return fmaxf(fabsf(dx), fabsf(dy)) < r;
     }
 }
+
+// Work counters of one search launch, in the order of sfc_search_stats (sfcoct.h).  Each
+// lane accumulates its own; warp-uniform events are counted by lane 0 alone.
+enum StatIndex {
+    kStWalks = 0,
+    kStExpansions,
+    kStBoxTests,
+    kStLeaves,
+    kStPointTests,
+    kStNeeded,
+    kStPassed,
+    kStWhole,
+    kStInserts,
+    kStCount
+};
+struct StatAcc {
+    unsigned long long v[kStCount];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < kStCount; ++i) v[i] = 0ull;
+    }
+    // The lanes of `lanes` (lane 0 and a prefix of the warp) call this once: their sums go
+    // to the device counters.
+    __device__ __forceinline__ void flush(unsigned long long* out, unsigned int lanes = 0xffffffffu) const {
+        const unsigned int lane = threadIdx.x & 31u;
+#pragma unroll
+        for (int i = 0; i < kStCount; ++i) {
+            unsigned long long x = v[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_down_sync(lanes, x, o);
+                if (lane + o < 32u && ((lanes >> (lane + o)) & 1u)) x += y;
+            }
+            if (lane == 0 && x) atomicAdd(out + i, x);
+        }
+    }
+};
 
 // Squared Euclidean distance used by kNN: (dx*dx + dy*dy) + dz*dz, rounded per operation.
 __device__ __forceinline__ float sq_dist(float dx, float dy, float dz) {

@@ -47,6 +47,7 @@ struct KnnArgs {
     // overflow found on the device earlier in the same stream)
     const unsigned int* skip;
     unsigned int skip_mask;
+    unsigned long long* stats;  // work counters (the STATS copies of the kernels)
 };
 
 __device__ __forceinline__ float box_lower_bound(const NodeBox& b, float cx, float cy, float cz) {
@@ -239,7 +240,8 @@ __device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
 // staged in shared memory with coalesced loads, and both the tests and the insertions read
 // them there.  Per chunk, pass 1 marks the points that beat each lane's current k-th pair
 // and pass 2 lets each lane insert its marked points.
-template <int KMAX>
+// STATS: also accumulate the work counters of sfc_search_stats.
+template <int KMAX, bool STATS = false>
 // the minimum resident blocks match what shared memory allows for each list size (the
 // register budget never becomes the tighter limit)
 __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX <= 16 ? 28 : (KMAX <= 32 ? 18 : 10)))
@@ -300,6 +302,11 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
     }
     gx *= inv; gy *= inv; gz *= inv;
 
+    StatAcc st;
+    if constexpr (STATS) {
+        st.zero();
+        st.v[kStWalks] = lane == 0;
+    }
     LaneHeap best;
     best.init(&heaps[warp][0][lane], k);
     auto key_of = [&](const float4& q) {
@@ -333,6 +340,10 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         const int nfill = min(k, static_cast<int>(2 * window));
         for (int t = 0; t < k; ++t) best.at(t) = t < nfill ? window_key(t) : kNoPair;
         best.heapify();
+        if constexpr (STATS) {
+            st.v[kStPointTests] += 2 * window;
+            st.v[kStNeeded] += active ? 2 * window : 0;
+        }
         for (int t0 = nfill; t0 < 2 * window; t0 += 32) {
             const int span = min(32, 2 * static_cast<int>(window) - t0);
             uint32_t cand = 0;
@@ -346,12 +357,16 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
                     if (sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)) <= kd) cand |= 1u << u;
                 }
             }
+            if constexpr (STATS) st.v[kStPassed] += __popc(cand);
             while (__ballot_sync(0xffffffffu, cand != 0)) {
                 if (cand) {
                     const int u = __ffs(cand) - 1;
                     cand &= cand - 1;
                     const uint64_t nk = window_key(t0 + u);
-                    if (nk < best.kth) best.insert(nk);
+                    if (nk < best.kth) {
+                        best.insert(nk);
+                        if constexpr (STATS) st.v[kStInserts] += 1;
+                    }
                 }
             }
         }
@@ -364,6 +379,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         const NodeBox rb = a.nodes[root];
         const int32_t rc = a.child[root];
         const unsigned int need = __ballot_sync(0xffffffffu, active && box_lower_bound(rb, c.x, c.y, c.z) <= best.kth_d2());
+        if constexpr (STATS) st.v[kStBoxTests] += 1;
         if (need) {
             if (lane == 0)
                 stack_e[warp][0] = make_int4(rc, __float_as_int(rb.lo.w), __float_as_int(rb.hi.w), static_cast<int>(need));
@@ -409,6 +425,10 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
                 }
             }
             const int nvalid = __popc(__ballot_sync(0xffffffffu, lane < 8 && (key >> 32) != 0xffffffffull));
+            if constexpr (STATS) {
+                st.v[kStExpansions] += lane == 0;
+                st.v[kStBoxTests] += nvalid;
+            }
             // push the farthest first so that the nearest is popped first
             for (int i = nvalid - 1; i >= 0; --i) {
                 const int ci = static_cast<int>(__shfl_sync(0xffffffffu, key, i) & 7ull);
@@ -431,6 +451,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         } else {
             const unsigned int needing = __ballot_sync(0xffffffffu, need);
             const uint32_t n_need = static_cast<uint32_t>(__popc(needing));
+            if constexpr (STATS) st.v[kStLeaves] += lane == 0;
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
                 const float4 mine = lane < m ? __ldg(&a.pts[base + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -468,12 +489,20 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
                     cand &= ~(run << static_cast<uint32_t>(lo - base));
                 }
                 if (!need) cand = 0;
+                if constexpr (STATS) {
+                    st.v[kStPointTests] += n_need < m ? n_need : m;  // per lane: transposed or not
+                    st.v[kStNeeded] += need ? m : 0u;
+                    st.v[kStPassed] += __popc(cand);
+                }
                 while (__ballot_sync(0xffffffffu, cand != 0)) {
                     if (cand) {
                         const int t = __ffs(cand) - 1;
                         cand &= cand - 1;
                         const uint64_t nk = key_of(buf[t]);
-                        if (nk < best.kth) best.insert(nk);
+                        if (nk < best.kth) {
+                            best.insert(nk);
+                            if constexpr (STATS) st.v[kStInserts] += 1;
+                        }
                     }
                 }
                 __syncwarp();
@@ -485,14 +514,20 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         best.store(a, out_base);
     }
     if (!guard_ok && lane == 0) atomicOr(a.err, kGuardTripped);
+    if constexpr (STATS) st.flush(a.stats);
 }
 
-template <int KMAX>
+template <int KMAX, bool STATS = false>
 __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
     const int64_t qi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (qi >= a.nq) return;
     const float4 c = a.q[qi];
     const uint32_t row = __float_as_uint(c.w);
+    StatAcc st;
+    if constexpr (STATS) {
+        st.zero();
+        st.v[kStWalks] = 1;
+    }
     BestList<KMAX> best;
     best.init(a.k);
     int32_t stk[kStackDepth];
@@ -508,9 +543,14 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
         const NodeBox b = a.nodes[node];
         const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
         if (start == end) continue;
+        if constexpr (STATS) st.v[kStBoxTests] += 1;
         if (box_lower_bound(b, c.x, c.y, c.z) > best.kth_d2()) continue;
         const int32_t fc = a.child[node];
         if (fc >= 0) {
+            if constexpr (STATS) {
+                st.v[kStExpansions] += 1;
+                st.v[kStBoxTests] += 8;
+            }
             uint64_t keys[8];
 #pragma unroll
             for (int ci = 0; ci < 8; ++ci) keys[ci] = child_order_key(a.nodes[fc + ci], c.x, c.y, c.z, ci);
@@ -529,24 +569,43 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
                     else guard_ok = false;
                 }
         } else {
+            if constexpr (STATS) {
+                st.v[kStLeaves] += 1;
+                st.v[kStPointTests] += end - start;
+                st.v[kStNeeded] += end - start;
+            }
             for (uint32_t j = start; j < end; ++j) {
                 const uint32_t id = a.perm[j];
                 const float4 p = a.pts[id];
                 const uint64_t nk = pair_key(sq_dist(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z)), id);
-                if (nk < best.kth) best.insert(nk);
+                if (nk < best.kth) {
+                    best.insert(nk);
+                    if constexpr (STATS) {
+                        st.v[kStPassed] += 1;
+                        st.v[kStInserts] += 1;
+                    }
+                }
             }
         }
     }
     best.store(a, row);
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
+    if constexpr (STATS) {
+        // the lanes of this warp that passed the entry test: a prefix of the warp
+        const int64_t live = a.nq - (qi - static_cast<int64_t>(lane_id()));
+        st.flush(a.stats, live >= 32 ? 0xffffffffu : (1u << live) - 1u);
+    }
 }
 
 template <int KMAX>
 static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) {
-    if (t->enc == SFC_ENC_NONE) {
+    constexpr int kWarps = knn_warps<KMAX>();
+    if (a.stats) {  // work counters on: the instrumented copies (same results)
+        if (t->enc == SFC_ENC_NONE) SFC_LAUNCH("knn", s, (k_knn_lane<KMAX, true>), grid_for(a.nq, 128), 128, 0, a);
+        else SFC_LAUNCH("knn", s, (k_knn_group<KMAX, true>), grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
+    } else if (t->enc == SFC_ENC_NONE) {
         SFC_LAUNCH("knn", s, k_knn_lane<KMAX>, grid_for(a.nq, 128), 128, 0, a);
     } else {
-        constexpr int kWarps = knn_warps<KMAX>();
         SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
     }
     return SFC_OK;
@@ -645,6 +704,7 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         a.ngroups = (rows + 31) / 32;
         a.skip = nullptr;
         a.skip_mask = 0;
+        a.stats = sfc::stats_counters();
         // curve neighbours per side for the seeding window: k (measured best from k = 8 to
         // 64 on the LiDAR tile; much narrower windows leave the walk many insertions)
         a.window = (!queries_xyz && t->enc != SFC_ENC_NONE) ? sfc::knn_default_window(k) : 0;

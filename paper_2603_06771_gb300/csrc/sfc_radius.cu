@@ -67,6 +67,7 @@ struct RadiusArgs {
     // overflow found on the device earlier in the same stream)
     const unsigned int* skip;
     unsigned int skip_mask;
+    unsigned long long* stats;          // work counters (the STATS copies of the count pass)
 };
 
 // A record header is (chunk start, chunk size <= 32) for a leaf chunk, or
@@ -107,10 +108,12 @@ __device__ __forceinline__ float axis_gap(float lo, float hi, float glo, float g
 // count pass counts runs, the fill writes them.
 constexpr uint32_t kNoRun = 0xffffffffu;
 
-template <int KERN, bool FILL, bool RUNS>
+// STATS: the count pass also accumulates the work counters of sfc_search_stats.
+template <int KERN, bool FILL, bool RUNS, bool STATS = false>
 // 18 two-warp fill blocks per SM (at most 56 registers) keep 36 warps resident: the fill
 // waits on memory more than the count pass does
 __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_radius_group(RadiusArgs a) {
+    static_assert(!STATS || (!FILL && !RUNS), "only the count pass of the CSR output is instrumented");
     constexpr int kRadiusWarps = radius_warps<FILL>();
     __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
     __shared__ uint32_t stack_w[kRadiusWarps][kStackDepth];  // lanes taking the node whole
@@ -140,6 +143,11 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     const int64_t row = row0 + __float_as_uint(c.w);
     const unsigned int below = lanes_below();
     const bool prune = a.prune != 0;
+    StatAcc st;
+    if constexpr (STATS) {
+        st.zero();
+        st.v[kStWalks] = lane == 0;
+    }
     uint32_t count = 0;
     int64_t out = (FILL && active) ? a.row_ptr[row] : 0;
     const int64_t out_end = (FILL && active) ? a.row_ptr[row + 1] : 0;
@@ -302,6 +310,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
         const NodeBox rb = a.nodes[root];
         const int32_t rc = a.child[root];
         const int cls = active ? classify_box<KERN>(rb, c.x, c.y, c.z, r, r2, prune) : 0;
+        if constexpr (STATS) st.v[kStBoxTests] += 1;
         const unsigned int p = __ballot_sync(0xffffffffu, cls == 1);
         const unsigned int w = __ballot_sync(0xffffffffu, cls == 2);
         if (p | w) {
@@ -331,6 +340,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
             const unsigned int whole = __ballot_sync(0xffffffffu, my_whole);
             const unsigned int partial = __ballot_sync(0xffffffffu, my_partial);
             if (whole) {
+                if constexpr (STATS) st.v[kStWhole] += my_whole ? end - start : 0u;
                 take_range(whole, start, end, my_whole);
                 if (recording) record(start, kRangeBit | end, my_whole ? 0xffffffffu : 0u);
                 if (my_whole) taken_below = end;
@@ -352,6 +362,10 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
                     chunk[warp][16 + lane] = make_float4(__int_as_float(cc), 0.f, 0.f, 0.f);
                 }
                 unsigned int kept = __ballot_sync(0xffffffffu, keep);
+                if constexpr (STATS) {
+                    st.v[kStExpansions] += lane == 0;
+                    st.v[kStBoxTests] += __popc(kept);
+                }
                 __syncwarp();
                 // push the last child first so that the first child is popped first
                 while (kept) {
@@ -383,6 +397,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
         } else {
             // a leaf: the lanes that reach its box test every point against their own centre
             const bool need = my_partial || my_whole;
+            if constexpr (STATS) st.v[kStLeaves] += lane == 0;
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
                 const float4 mine = lane < m ? __ldg(&a.pts[base + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -398,6 +413,11 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
                 }
                 __syncwarp();
                 if (!need) hits = 0;
+                if constexpr (STATS) {
+                    st.v[kStPointTests] += m;
+                    st.v[kStNeeded] += my_partial ? m : 0u;
+                    st.v[kStPassed] += __popc(hits);
+                }
                 if (recording && __ballot_sync(0xffffffffu, hits != 0)) record(base, m, hits);
                 take_hits(hits, static_cast<int32_t>(__float_as_uint(mine.w)), base);
             }
@@ -407,16 +427,23 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     if (!FILL && active) a.counts[row] = count;
     if (recording && lane == 0) a.rec_count[group] = rec_overflow ? kRecordsOverflow : nrec;
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
+    if constexpr (STATS) st.flush(a.stats);
 }
 
 // One centre per thread, its own depth-first walk; points through the permutation.
-template <int KERN, bool FILL, bool RUNS>
+template <int KERN, bool FILL, bool RUNS, bool STATS = false>
 __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
+    static_assert(!STATS || (!FILL && !RUNS), "only the count pass of the CSR output is instrumented");
     const int64_t qi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (qi >= a.nq) return;
     const float4 c = a.q[qi];
     const uint32_t row = __float_as_uint(c.w);
     const bool prune = a.prune != 0;
+    StatAcc st;
+    if constexpr (STATS) {
+        st.zero();
+        st.v[kStWalks] = 1;
+    }
     int32_t stk[kStackDepth];
     int sp = 1;
     stk[0] = 0;
@@ -449,10 +476,12 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
         const uint32_t start = __float_as_uint(b.lo.w), end = __float_as_uint(b.hi.w);
         if (start == end) continue;
         const int cls = classify_box<KERN>(b, c.x, c.y, c.z, a.r, a.r2, prune);
+        if constexpr (STATS) st.v[kStBoxTests] += 1;
         if (cls == 0) continue;
         const int32_t fc = a.child[node];
         if (fc >= 0) {
             if (cls == 2) {
+                if constexpr (STATS) st.v[kStWhole] += end - start;
                 if (RUNS) {
                     add_run(start, end);
                     continue;
@@ -467,16 +496,23 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
                 count += end - start;
                 continue;
             }
+            if constexpr (STATS) st.v[kStExpansions] += 1;
             if (sp + 8 <= kStackDepth) {
                 for (int k = 7; k >= 0; --k) stk[sp++] = fc + k;
             } else {
                 guard_ok = false;
             }
         } else {
+            if constexpr (STATS) {
+                st.v[kStLeaves] += 1;
+                st.v[kStPointTests] += end - start;
+                st.v[kStNeeded] += cls == 1 ? end - start : 0u;
+            }
             for (uint32_t j = start; j < end; ++j) {
                 const uint32_t id = a.perm[j];
                 const float4 p = a.pts[id];
                 if (kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z), a.r, a.r2)) {
+                    if constexpr (STATS) st.v[kStPassed] += 1;
                     if (RUNS) {
                         add_run(j, j + 1);
                         continue;
@@ -496,6 +532,42 @@ __global__ void __launch_bounds__(128) k_radius_lane(RadiusArgs a) {
     }
     if (!FILL) a.counts[row] = count;
     if (!guard_ok) atomicOr(a.err, kGuardTripped);
+    if constexpr (STATS) {
+        // the lanes of this warp that passed the entry test: a prefix of the warp
+        const int64_t live = a.nq - (qi - static_cast<int64_t>(lane_id()));
+        st.flush(a.stats, live >= 32 ? 0xffffffffu : (1u << live) - 1u);
+    }
+}
+
+// the instrumented count pass (work counters on): same decisions, same output
+static sfc_status launch_count_stats(const Octree* t, RadiusArgs& a, int kern, const char* name, cudaStream_t s) {
+    if (t->enc == SFC_ENC_NONE) {
+        const unsigned int grid = grid_for(a.nq, 128);
+        switch (kern) {
+        case SFC_SPHERE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SPHERE, false, false, true>), grid, 128, 0, a); break;
+        case SFC_CIRCLE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CIRCLE, false, false, true>), grid, 128, 0, a); break;
+        case SFC_CUBE: SFC_LAUNCH(name, s, (k_radius_lane<SFC_CUBE, false, false, true>), grid, 128, 0, a); break;
+        default: SFC_LAUNCH(name, s, (k_radius_lane<SFC_SQUARE, false, false, true>), grid, 128, 0, a); break;
+        }
+    } else {
+        constexpr int kWarps = radius_warps<false>();
+        const unsigned int grid = grid_for(a.ngroups, kWarps);
+        switch (kern) {
+        case SFC_SPHERE:
+            SFC_LAUNCH(name, s, (k_radius_group<SFC_SPHERE, false, false, true>), grid, kWarps * 32, 0, a);
+            break;
+        case SFC_CIRCLE:
+            SFC_LAUNCH(name, s, (k_radius_group<SFC_CIRCLE, false, false, true>), grid, kWarps * 32, 0, a);
+            break;
+        case SFC_CUBE:
+            SFC_LAUNCH(name, s, (k_radius_group<SFC_CUBE, false, false, true>), grid, kWarps * 32, 0, a);
+            break;
+        default:
+            SFC_LAUNCH(name, s, (k_radius_group<SFC_SQUARE, false, false, true>), grid, kWarps * 32, 0, a);
+            break;
+        }
+    }
+    return SFC_OK;
 }
 
 template <bool FILL, bool RUNS>
@@ -503,6 +575,9 @@ static sfc_status launch_search_as(const Octree* t, RadiusArgs& a, int kern, cud
     if (a.nq == 0) return SFC_OK;
     const char* name = RUNS ? (FILL ? "radius_ranges_fill" : "radius_ranges_count")
                             : (FILL ? "radius_fill" : "radius_count");
+    if constexpr (!FILL && !RUNS) {
+        if (a.stats) return launch_count_stats(t, a, kern, name, s);
+    }
     if (t->enc == SFC_ENC_NONE) {
         const unsigned int grid = grid_for(a.nq, 128);
         switch (kern) {
@@ -558,6 +633,7 @@ static RadiusArgs make_args(const Octree* t, const float4* q4, int64_t rows, flo
     a.skip_mask = 0;
     a.runs = nullptr;
     a.out_runs = 0;
+    a.stats = stats_counters();
     return a;
 }
 

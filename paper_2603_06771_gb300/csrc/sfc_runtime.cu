@@ -26,6 +26,12 @@ void record_cuda_error(cudaError_t e, const char* where) {
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<bool> g_prof_on{false};
 static std::mutex g_prof_mu;
+static std::atomic<bool> g_stats_on{false};
+static std::mutex g_stats_mu;
+static unsigned long long* g_stats = nullptr;  // kStCount counters, kept for the process
+
+unsigned long long* stats_counters() { return g_stats_on.load(std::memory_order_relaxed) ? g_stats : nullptr; }
+
 struct ProfRecord {
     std::string name;
     cudaEvent_t start, stop;
@@ -458,6 +464,34 @@ sfc_status sfc_set_allocator(sfc_alloc_fn alloc, sfc_free_fn free_fn, void* ctx)
 }
 
 int64_t sfc_live_allocations(void) { return sfc::g_live.load(); }
+
+sfc_status sfc_stats_enable(int32_t on) {
+    std::lock_guard<std::mutex> g(sfc::g_stats_mu);
+    if (on) {
+        if (!sfc::g_stats) {
+            void* p = nullptr;
+            SFC_CUDA(cudaMalloc(&p, sizeof(unsigned long long) * sfc::kStCount));
+            sfc::g_stats = static_cast<unsigned long long*>(p);
+        }
+        SFC_CUDA(cudaDeviceSynchronize());
+        SFC_CUDA(cudaMemset(sfc::g_stats, 0, sizeof(unsigned long long) * sfc::kStCount));
+        SFC_CUDA(cudaDeviceSynchronize());
+    }
+    sfc::g_stats_on.store(on != 0);
+    return SFC_OK;
+}
+
+sfc_status sfc_stats_read(sfc_search_stats* out) {
+    if (!out) return SFC_ERR_INVALID;
+    static_assert(sizeof(sfc_search_stats) == sizeof(unsigned long long) * sfc::kStCount,
+                  "one counter per field");
+    std::lock_guard<std::mutex> g(sfc::g_stats_mu);
+    memset(out, 0, sizeof *out);
+    if (!sfc::g_stats) return SFC_OK;
+    SFC_CUDA(cudaDeviceSynchronize());
+    SFC_CUDA(cudaMemcpy(out, sfc::g_stats, sizeof *out, cudaMemcpyDeviceToHost));
+    return SFC_OK;
+}
 
 sfc_status sfc_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> g(sfc::g_prof_mu);
