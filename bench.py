@@ -52,18 +52,18 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 203560704 + 1250418176, "sha256": "e13aec15d818d2dd7dc7cc9baffb40afead4f89cb0ff07c1073f6ebb10566f7f"},
-    "radius_fill": {"bytes_per_launch": 3077275648 + 4252898304, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
-    "radius_count": {"bytes_per_launch": 325291776 + 925327360, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
+    "knn": {"bytes_per_launch": 203978752 + 1250165760, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
+    "radius_fill": {"bytes_per_launch": 3076853248 + 4252443392, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
+    "radius_count": {"bytes_per_launch": 324239872 + 925502976, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
 }
 
 
-# warp instructions per group of 32 centres of the dominant kernels, from the full ncu set
-# of the 2M-point tile (profiles/search_kernels_full_lidar_tile_2M.md), keyed like the traffic
+# warp instructions per group of 32 centres of the dominant kernels (ncu
+# smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "e13aec15d818d2dd7dc7cc9baffb40afead4f89cb0ff07c1073f6ebb10566f7f"},
-    "radius_count": {"warp_inst": 839805701 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
-    "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "391f79b0673a156977a16f998c00310a0b15e7e7d114a54735471a7a35c2b5ca"},
+    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
+    "radius_count": {"warp_inst": 839805701 / 62500, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
+    "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
