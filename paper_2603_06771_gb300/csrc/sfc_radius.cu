@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     __shared__ int4 stack_e[kRadiusWarps][kStackDepth];      // first child, start, end, undecided lanes
     __shared__ uint32_t stack_w[kRadiusWarps][kStackDepth];  // lanes taking the node whole
     __shared__ float4 chunk[kRadiusWarps][32];
+    __shared__ float4 centre[FILL ? 1 : kRadiusWarps][32];  // count pass: the warp's centres
     const unsigned int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const int64_t group = static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     const bool active = qi < q_end;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t row = row0 + __float_as_uint(c.w);
+    if constexpr (!FILL) centre[warp][lane] = c;  // read by other lanes after the next __syncwarp
     const unsigned int below = lanes_below();
     const bool prune = a.prune != 0;
     StatAcc st;
@@ -397,24 +399,45 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
         } else {
             // a leaf: the lanes that reach its box test every point against their own centre
             const bool need = my_partial || my_whole;
+            // lanes whose kernel holds for the whole leaf box take every point untested (its
+            // farthest corner passed, so every point passes: step 1a); the others test
+            const unsigned int testing = __ballot_sync(0xffffffffu, my_partial);
+            const uint32_t n_test = static_cast<uint32_t>(__popc(testing));
             if constexpr (STATS) st.v[kStLeaves] += lane == 0;
             for (uint32_t base = start; base < end; base += 32) {
                 const uint32_t m = min(32u, end - base);
                 const float4 mine = lane < m ? __ldg(&a.pts[base + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                chunk[warp][lane] = mine;
-                __syncwarp();
                 uint32_t hits = 0;
+                const bool transposed = !FILL && 4 * n_test <= 3 * m;
+                if (transposed) {
+                    // few centres test this chunk: every lane holds a point and the testing
+                    // centres come in turn, each lane's hit mask is one ballot
+                    unsigned int todo = testing;
+                    while (todo) {
+                        const int l = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const float4 cl = centre[warp][l];
+                        const bool in = lane < m && kernel_holds<KERN>(__fsub_rn(mine.x, cl.x), __fsub_rn(mine.y, cl.y),
+                                                                       __fsub_rn(mine.z, cl.z), r, r2);
+                        const uint32_t b = __ballot_sync(0xffffffffu, in);
+                        if (lane == static_cast<unsigned int>(l)) hits = b;
+                    }
+                } else {
+                    chunk[warp][lane] = mine;
+                    __syncwarp();
 #pragma unroll 8
-                for (uint32_t t = 0; t < m; ++t) {
-                    const float4 p = chunk[warp][t];
-                    const bool in = kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y), __fsub_rn(p.z, c.z),
-                                                       r, r2);
-                    hits |= static_cast<uint32_t>(in) << t;
+                    for (uint32_t t = 0; t < m; ++t) {
+                        const float4 p = chunk[warp][t];
+                        const bool in = kernel_holds<KERN>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y),
+                                                           __fsub_rn(p.z, c.z), r, r2);
+                        hits |= static_cast<uint32_t>(in) << t;
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
+                if (my_whole) hits = m >= 32u ? 0xffffffffu : (1u << m) - 1u;
                 if (!need) hits = 0;
                 if constexpr (STATS) {
-                    st.v[kStPointTests] += m;
+                    st.v[kStPointTests] += transposed ? n_test : m;
                     st.v[kStNeeded] += my_partial ? m : 0u;
                     st.v[kStPassed] += __popc(hits);
                 }
