@@ -53,8 +53,8 @@ L2_FLUSH_BYTES = 512 << 20
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
     "knn": {"bytes_per_launch": 203978752 + 1250165760, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
-    "radius_fill": {"bytes_per_launch": 3076853248 + 4252443392, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
-    "radius_count": {"bytes_per_launch": 324239872 + 925502976, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
+    "radius_fill": {"bytes_per_launch": 3076345600 + 4251524864, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "radius_count": {"bytes_per_launch": 323007744 + 920743680, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
 
 
@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
     "knn": {"warp_inst": 1633391437 / 62500, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
-    "radius_count": {"warp_inst": 839805701 / 62500, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
-    "radius_fill": {"warp_inst": 691422052 / 62500, "sha256": "e5f3d552774a23e23ec5b784ca4a509655e479e1851ecb612a87fbbe95ba41d1"},
+    "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "radius_fill": {"warp_inst": 693607714 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
@@ -88,6 +88,8 @@ def parse_args(argv=None):
                     help="neighbour ids (CSR) or runs of sorted positions (range output)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-counters", action="store_true",
+                    help="skip the untimed work-counter pass after the timed region")
     ap.add_argument("--clocks-csv", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--workload", choices=["lidar_tile_10M", "batch256", "serving", "sweep"], default="lidar_tile_10M")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -848,16 +850,17 @@ def main(argv=None):
 
     # candidate tests of the two search kernels (instrumented copies, run once, untimed)
     tests = {}
-    t = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
     sm_mhz = clk.get("sm_mhz") if clk else None
-    if cfg["radius"].get("output") != "ranges" and "radius_count" in prof:
-        c = search_counters(sfc, lambda: sfc.radius_count(t, None, cfg["radius"]["r"], cfg["radius"]["kernel"]))
-        tests["radius_count"] = alu_side(c, cfg["radius"]["kernel"], prof["radius_count"][1] /
-                                         prof["radius_count"][0], sm_mhz)
-    if "knn" in prof:
-        c = search_counters(sfc, lambda: sfc.knn(t, None, k))
-        tests["knn"] = alu_side(c, "knn", prof["knn"][1] / prof["knn"][0], sm_mhz)
-    t.free()
+    if not args.no_counters:
+        t = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
+        if cfg["radius"].get("output") != "ranges" and "radius_count" in prof:
+            c = search_counters(sfc, lambda: sfc.radius_count(t, None, cfg["radius"]["r"], cfg["radius"]["kernel"]))
+            tests["radius_count"] = alu_side(c, cfg["radius"]["kernel"], prof["radius_count"][1] /
+                                             prof["radius_count"][0], sm_mhz)
+        if "knn" in prof:
+            c = search_counters(sfc, lambda: sfc.knn(t, None, k))
+            tests["knn"] = alu_side(c, "knn", prof["knn"][1] / prof["knn"][0], sm_mhz)
+        t.free()
     if roof is not None and dom_name in tests and "fp32_frac" in tests[dom_name]:
         a = tests[dom_name]
         roof["alu"] = {"achieved": a["fp32_ops_per_s"], "peak": a["fp32_peak"], "unit": "FP32 op/s",
