@@ -1,0 +1,37 @@
+"""Host arithmetic of the benchmark line (no GPU): the roofline's algorithmic bytes and the
+ALU side computed from the work counters."""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_per_launch():
+    n, nnz, k = 10_000_000, 878_570_600, 16
+    assert bench.algorithmic_bytes("knn", n, nnz, k) == 16 * n + 8 * n * k == 1_440_000_000
+    assert bench.algorithmic_bytes("radius_fill", n, nnz, k) == 16 * n + 8 * (n + 1) + 4 * nnz
+    assert bench.algorithmic_bytes("radius_count", n, nnz, k) == 16 * n
+    assert bench.algorithmic_bytes("not_a_kernel", n, nnz, k) is None
+
+
+def test_alu_side_against_the_fp32_lanes():
+    counters = {"walks": 10, "expansions": 0, "box_tests": 0, "leaves": 0, "point_tests": 2_000_000_000,
+                "needed_tests": 500_000_000, "passed": 0, "whole": 0, "inserts": 0}
+    a = bench.alu_side(counters, "sphere", 4.0, 2070.0)
+    assert a["tests_per_s"] == pytest.approx(5e11)
+    assert a["needed_tests_per_s"] == pytest.approx(1.25e11)
+    assert a["fp32_peak"] == pytest.approx(152 * 128 * 2070e6)
+    assert a["fp32_frac"] == pytest.approx(5e11 * 9 / (152 * 128 * 2070e6))
+    # without a clock sample there is no peak to divide by
+    assert "fp32_frac" not in bench.alu_side(counters, "square", 4.0, None)
+
+
+def test_every_search_kind_has_an_operation_count():
+    assert set(bench.FP32_OPS_PER_TEST) == {"sphere", "circle", "cube", "square", "knn"}
+    # sphere / kNN: 3 differences, 3 products, 2 sums and the comparison; the 2D and L-inf
+    # kernels drop the z product or use maxima
+    assert bench.FP32_OPS_PER_TEST["sphere"] == bench.FP32_OPS_PER_TEST["knn"] == 9
+    assert bench.FP32_OPS_PER_TEST["square"] < bench.FP32_OPS_PER_TEST["circle"] < 9
