@@ -52,16 +52,16 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 203978752 + 1250165760, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
-    "radius_fill": {"bytes_per_launch": 3076345600 + 4251524864, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
-    "radius_count": {"bytes_per_launch": 323007744 + 920743680, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "knn": {"bytes_per_launch": 203606016 + 1250454528, "sha256": "5437ba568a1146ea4566cf03f956c83b179949800ed8df1d5fd8dfaf6b2d31c9"},
+    "radius_fill": {"bytes_per_launch": 3077817344 + 4252774144, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "radius_count": {"bytes_per_launch": 323075072 + 921261824, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1633391437 / 62500, "sha256": "7d222d57f263c29f94312348d7637a150b976298cfaa79fe800dbd7849dc627c"},
+    "knn": {"warp_inst": 1632891437 / 62500, "sha256": "5437ba568a1146ea4566cf03f956c83b179949800ed8df1d5fd8dfaf6b2d31c9"},
     "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
     "radius_fill": {"warp_inst": 693607714 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
