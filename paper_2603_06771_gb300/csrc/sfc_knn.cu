@@ -131,44 +131,60 @@ struct LaneHeap {
         for (int s = 0; s < k; ++s) at(s) = kNoPair;
         kth = kNoPair;
     }
+    // the largest of the children c0 .. c0 + D - 1 (those below `size`; c0 < size) and its slot
+    __device__ __forceinline__ uint64_t max_child(int c0, int size, int* c) const {
+        if constexpr (D == 2) {
+            uint64_t cv = at(c0);
+            *c = c0;
+            if (c0 + 1 < size) {
+                const uint64_t rv = at(c0 + 1);
+                if (rv > cv) {
+                    *c = c0 + 1;
+                    cv = rv;
+                }
+            }
+            return cv;
+        } else {
+            // absent children read as the smallest key, which never moves up
+            const uint64_t v0 = at(c0);
+            const uint64_t v1 = c0 + 1 < size ? at(c0 + 1) : 0ull;
+            const uint64_t v2 = c0 + 2 < size ? at(c0 + 2) : 0ull;
+            const uint64_t v3 = c0 + 3 < size ? at(c0 + 3) : 0ull;
+            const bool a = v1 > v0, b = v3 > v2;
+            const uint64_t m01 = a ? v1 : v0, m23 = b ? v3 : v2;
+            const bool hi = m23 > m01;
+            *c = hi ? (b ? c0 + 3 : c0 + 2) : (a ? c0 + 1 : c0);
+            return hi ? m23 : m01;
+        }
+    }
     // place x at slot pos of the heap of the first `size` slots and restore the order below it
     __device__ __forceinline__ void sift_down(uint64_t x, int size, int pos = 0) {
         for (;;) {
             const int c0 = D * pos + 1;
             if (c0 >= size) break;
             int c;
-            uint64_t cv;
-            if constexpr (D == 2) {
-                c = c0;
-                cv = at(c0);
-                if (c0 + 1 < size) {
-                    const uint64_t rv = at(c0 + 1);
-                    if (rv > cv) {
-                        c = c0 + 1;
-                        cv = rv;
-                    }
-                }
-            } else {
-                // absent children read as the smallest key, which never moves up
-                const uint64_t v0 = at(c0);
-                const uint64_t v1 = c0 + 1 < size ? at(c0 + 1) : 0ull;
-                const uint64_t v2 = c0 + 2 < size ? at(c0 + 2) : 0ull;
-                const uint64_t v3 = c0 + 3 < size ? at(c0 + 3) : 0ull;
-                const bool a = v1 > v0, b = v3 > v2;
-                const uint64_t m01 = a ? v1 : v0, m23 = b ? v3 : v2;
-                const bool hi = m23 > m01;
-                cv = hi ? m23 : m01;
-                c = hi ? (b ? c0 + 3 : c0 + 2) : (a ? c0 + 1 : c0);
-            }
+            const uint64_t cv = max_child(c0, size, &c);
             if (cv <= x) break;
             at(pos) = cv;
             pos = c;
         }
         at(pos) = x;
     }
-    __device__ __forceinline__ void insert(uint64_t nk) {  // requires nk < kth
-        sift_down(nk, k);
-        kth = at(0);
+    // replace the root (the k-th pair) by nk < kth; the new root, the larger of nk and the
+    // root's largest child, is known before the rest of the sift and stays in a register
+    __device__ __forceinline__ void insert(uint64_t nk) {
+        if (k > 1) {
+            int c;
+            const uint64_t cv = max_child(1, k, &c);
+            if (cv > nk) {
+                at(0) = cv;
+                kth = cv;
+                sift_down(nk, k, c);
+                return;
+            }
+        }
+        at(0) = nk;
+        kth = nk;
     }
     // the k slots hold arbitrary pairs: restore the heap order bottom-up
     __device__ __forceinline__ void heapify() {
@@ -230,6 +246,14 @@ __device__ __forceinline__ uint64_t child_order_key(const NodeBox& cb, float gx,
     const bool empty = __float_as_uint(cb.lo.w) == __float_as_uint(cb.hi.w);
     const uint32_t bound = empty ? 0xffffffffu : float_to_ordered(box_lower_bound(cb, gx, gy, gz));
     return (static_cast<uint64_t>(bound) << 32) | static_cast<uint32_t>(ci);
+}
+
+// The same order in 32 bits for the group walk: the bound's order-preserving image with
+// its three low bits replaced by the child number (bounds within 8 ulps may swap places,
+// which changes the visiting order only); 0xffffffff marks an empty child.
+__device__ __forceinline__ uint32_t child_order_key32(const NodeBox& cb, float gx, float gy, float gz, int ci) {
+    if (__float_as_uint(cb.lo.w) == __float_as_uint(cb.hi.w)) return 0xffffffffu;
+    return (float_to_ordered(box_lower_bound(cb, gx, gy, gz)) & ~7u) | static_cast<uint32_t>(ci);
 }
 
 // Squared distance bound between a node box and the box of a group of centres; no
@@ -427,32 +451,32 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
             // reachable children, nearest to the group centre first (bitonic sort, lanes 0..7)
             NodeBox cb;
             int32_t cc = -1;
-            uint64_t key = ~0ull;
+            uint32_t key = 0xffffffffu;
             if (lane < 8) {
                 cb = a.nodes[fc + lane];
                 cc = a.child[fc + lane];
                 if (group_lower_bound(cb, glx, gly, glz, ghx, ghy, ghz) <= mkd)
-                    key = child_order_key(cb, gx, gy, gz, static_cast<int>(lane));
+                    key = child_order_key32(cb, gx, gy, gz, static_cast<int>(lane));
             }
 #pragma unroll
             for (int size = 2; size <= 8; size <<= 1) {
 #pragma unroll
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const uint64_t other = __shfl_xor_sync(0xffffffffu, key, stride);
+                    const uint32_t other = __shfl_xor_sync(0xffffffffu, key, stride);
                     const bool ascending = (lane & size) == 0;
                     const bool lower = (lane & stride) == 0;
                     const bool take = (lower == ascending) ? (other < key) : (other > key);
                     if (lane < 8 && take) key = other;
                 }
             }
-            const int nvalid = __popc(__ballot_sync(0xffffffffu, lane < 8 && (key >> 32) != 0xffffffffull));
+            const int nvalid = __popc(__ballot_sync(0xffffffffu, lane < 8 && key != 0xffffffffu));
             if constexpr (STATS) {
                 st.v[kStExpansions] += lane == 0;
                 st.v[kStBoxTests] += nvalid;
             }
             // push the farthest first so that the nearest is popped first
             for (int i = nvalid - 1; i >= 0; --i) {
-                const int ci = static_cast<int>(__shfl_sync(0xffffffffu, key, i) & 7ull);
+                const int ci = static_cast<int>(__shfl_sync(0xffffffffu, key, i) & 7u);
                 const NodeBox b = shfl_node(cb, ci);
                 const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
                 const unsigned int cneed =
