@@ -52,16 +52,16 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 203606016 + 1250454528, "sha256": "5437ba568a1146ea4566cf03f956c83b179949800ed8df1d5fd8dfaf6b2d31c9"},
-    "radius_fill": {"bytes_per_launch": 3077817344 + 4252774144, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
-    "radius_count": {"bytes_per_launch": 323075072 + 921261824, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "knn": {"bytes_per_launch": 204402176 + 1250188800, "sha256": "1205d7f0a5de23693afa81032deca3382ea2a6c761baea031f37c81ac8fd8554"},
+    "radius_fill": {"bytes_per_launch": 3076770304 + 4252159744, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "radius_count": {"bytes_per_launch": 323224576 + 921416960, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1632891437 / 62500, "sha256": "5437ba568a1146ea4566cf03f956c83b179949800ed8df1d5fd8dfaf6b2d31c9"},
+    "knn": {"warp_inst": 1553060916 / 62500, "sha256": "1205d7f0a5de23693afa81032deca3382ea2a6c761baea031f37c81ac8fd8554"},
     "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
     "radius_fill": {"warp_inst": 693607714 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
