@@ -476,11 +476,12 @@ typedef struct {
 
 /* on != 0 zeroes the counters (synchronising the device) and makes the searches launch an
  * instrumented copy of their kernels: the same results, more registers and instructions,
- * so never time a search while counting.  0 stops counting.  SFC_ERR_CUDA if the
- * counters cannot be allocated. */
+ * so never time a search while counting.  The counters live on the device current at
+ * this call; searches launched on another device are not counted.  0 stops counting.
+ * SFC_ERR_CUDA if the counters cannot be allocated. */
 sfc_status sfc_stats_enable(int32_t on);
-/* Synchronises the device and copies the counters into *out (all zero if counting was
- * never enabled).  SFC_ERR_INVALID for out == NULL. */
+/* Synchronises the counters' device and copies the counters into *out (all zero if
+ * counting was never enabled).  SFC_ERR_INVALID for out == NULL. */
 sfc_status sfc_stats_read(sfc_search_stats* out);
 
 #ifdef __cplusplus

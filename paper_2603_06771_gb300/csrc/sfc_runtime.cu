@@ -29,8 +29,18 @@ static std::mutex g_prof_mu;
 static std::atomic<bool> g_stats_on{false};
 static std::mutex g_stats_mu;
 static unsigned long long* g_stats = nullptr;  // kStCount counters, kept for the process
+static int g_stats_device = -1;                // the device that holds them
 
-unsigned long long* stats_counters() { return g_stats_on.load(std::memory_order_relaxed) ? g_stats : nullptr; }
+// counting happens on the counters' device only (a search on another device is not counted)
+unsigned long long* stats_counters() {
+    if (!g_stats_on.load(std::memory_order_relaxed)) return nullptr;
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return d == g_stats_device ? g_stats : nullptr;
+}
 
 struct ProfRecord {
     std::string name;
@@ -468,10 +478,21 @@ int64_t sfc_live_allocations(void) { return sfc::g_live.load(); }
 sfc_status sfc_stats_enable(int32_t on) {
     std::lock_guard<std::mutex> g(sfc::g_stats_mu);
     if (on) {
+        int dev = -1;
+        SFC_CUDA(cudaGetDevice(&dev));
+        if (sfc::g_stats && dev != sfc::g_stats_device) {  // counting moves to the current device
+            SFC_CUDA(cudaSetDevice(sfc::g_stats_device));
+            const cudaError_t e = cudaDeviceSynchronize();
+            cudaFree(sfc::g_stats);
+            sfc::g_stats = nullptr;
+            SFC_CUDA(cudaSetDevice(dev));
+            SFC_CUDA(e);
+        }
         if (!sfc::g_stats) {
             void* p = nullptr;
             SFC_CUDA(cudaMalloc(&p, sizeof(unsigned long long) * sfc::kStCount));
             sfc::g_stats = static_cast<unsigned long long*>(p);
+            sfc::g_stats_device = dev;
         }
         SFC_CUDA(cudaDeviceSynchronize());
         SFC_CUDA(cudaMemset(sfc::g_stats, 0, sizeof(unsigned long long) * sfc::kStCount));
@@ -488,8 +509,13 @@ sfc_status sfc_stats_read(sfc_search_stats* out) {
     std::lock_guard<std::mutex> g(sfc::g_stats_mu);
     memset(out, 0, sizeof *out);
     if (!sfc::g_stats) return SFC_OK;
-    SFC_CUDA(cudaDeviceSynchronize());
-    SFC_CUDA(cudaMemcpy(out, sfc::g_stats, sizeof *out, cudaMemcpyDeviceToHost));
+    int dev = -1;
+    SFC_CUDA(cudaGetDevice(&dev));
+    SFC_CUDA(cudaSetDevice(sfc::g_stats_device));  // wait for the work of the counters' device
+    const cudaError_t e1 = cudaDeviceSynchronize();
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaMemcpy(out, sfc::g_stats, sizeof *out, cudaMemcpyDeviceToHost) : e1;
+    SFC_CUDA(cudaSetDevice(dev));
+    SFC_CUDA(e2);
     return SFC_OK;
 }
 
