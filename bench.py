@@ -52,7 +52,7 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 204402176 + 1250188800, "sha256": "1205d7f0a5de23693afa81032deca3382ea2a6c761baea031f37c81ac8fd8554"},
+    "knn": {"bytes_per_launch": 204402176 + 1250188800, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
     "radius_fill": {"bytes_per_launch": 3076770304 + 4252159744, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
     "radius_count": {"bytes_per_launch": 323224576 + 921416960, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }
@@ -61,7 +61,7 @@ NCU_TRAFFIC = {
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1553060916 / 62500, "sha256": "1205d7f0a5de23693afa81032deca3382ea2a6c761baea031f37c81ac8fd8554"},
+    "knn": {"warp_inst": 1553060916 / 62500, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
     "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
     "radius_fill": {"warp_inst": 693607714 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
 }

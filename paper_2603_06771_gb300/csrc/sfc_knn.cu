@@ -1,8 +1,9 @@
 // sfc_knn.cu - k nearest neighbours over the linear octree (section 3.3).
 //
 // The paper pops octants and points from one priority queue ordered by distance.  Here
-// each centre keeps its k best (squared distance, original index) pairs in registers,
-// sorted, and the octree is walked depth first with the children of a node visited
+// each centre keeps its k best (squared distance, original index) pairs (a max-heap in
+// shared memory for the warp-group walk, a sorted register list for the walk of one
+// centre), and the octree is walked depth first with the children of a node visited
 // nearest first; a node is entered only while its box could still hold a better pair.
 // The result is the same exact set, in the same (d2, index) order:
 //   - an octant's lower bound is the squared distance to its box point nearest to the
