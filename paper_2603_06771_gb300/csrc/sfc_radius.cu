@@ -231,12 +231,29 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
                 hits = 0;
             }
             unsigned int todo = __ballot_sync(0xffffffffu, hits != 0);
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const uint32_t h = __shfl_sync(0xffffffffu, hits, src);
-                const int64_t o = __shfl_sync(0xffffffffu, out, src);
-                if ((h >> lane) & 1u) a.cols[o + __popc(h & below)] = my_id;
+            if (todo) {
+                // two rows per round: lanes 0-15 write one lane's hits, lanes 16-31 the next
+                // one's; lane h of a half writes the chunk points h and h + 16, whose ids it
+                // takes once per chunk
+                const unsigned int hl = lane & 15u;
+                const bool upper = lane >= 16u;
+                const int32_t id_lo = __shfl_sync(0xffffffffu, my_id, static_cast<int>(hl));
+                const int32_t id_hi = __shfl_sync(0xffffffffu, my_id, static_cast<int>(hl + 16u));
+                const uint32_t below_lo = (1u << hl) - 1u;
+                const uint32_t below_hi = (below_lo << 16) | 0xffffu;
+                while (todo) {
+                    const int s0 = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int s1 = __ffs(todo) - 1;  // -1 when no second row is left
+                    todo &= todo - 1;
+                    const int src = upper ? s1 : s0;
+                    const uint32_t h = __shfl_sync(0xffffffffu, hits, src < 0 ? 0 : src);
+                    const int64_t o = __shfl_sync(0xffffffffu, out, src < 0 ? 0 : src);
+                    if (src >= 0) {
+                        if ((h >> hl) & 1u) a.cols[o + __popc(h & below_lo)] = id_lo;
+                        if ((h >> (hl + 16u)) & 1u) a.cols[o + __popc(h & below_hi)] = id_hi;
+                    }
+                }
             }
             out += __popc(hits);
         }
