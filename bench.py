@@ -52,9 +52,9 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 204402176 + 1250188800, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
-    "radius_fill": {"bytes_per_launch": 3076770304 + 4252159744, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
-    "radius_count": {"bytes_per_launch": 323224576 + 921416960, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "knn": {"bytes_per_launch": 203176960 + 1250478592, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
+    "radius_fill": {"bytes_per_launch": 3128745216 + 4302570240, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
+    "radius_count": {"bytes_per_launch": 322941696 + 921340672, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
 }
 
 
@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
     "knn": {"warp_inst": 1553060916 / 62500, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
-    "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
-    "radius_fill": {"warp_inst": 693607714 / 62500, "sha256": "5e0e8141b147c5c992f51d84cfc8579958b24f04b06f0d43e775e03d8a3fd3ab"},
+    "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
+    "radius_fill": {"warp_inst": 627950257 / 62500, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
