@@ -110,15 +110,15 @@ sfc_status run_single(sfc_server_s* S, Request& q, cudaStream_t s) {
     o.leaf_capacity = S->o.leaf_capacity;
     float* dpts = nullptr;
     float* dq = nullptr;
-    SFC_TRY(sfc::dev_alloc(&dpts, 3 * r.n_points, s));
+    sfc::Scratch scratch(s);  // the device copies of the points and centres, freed in stream order on return
+    SFC_TRY(scratch.alloc(&dpts, 3 * r.n_points));
     if (r.n_points > 0)
         SFC_CUDA(cudaMemcpyAsync(dpts, r.points_xyz, sizeof(float) * 3 * r.n_points, cudaMemcpyHostToDevice, s));
-    sfc_status st = octree_build(dpts, r.n_points, S->o.enc, &o, s, &q.tree);
-    sfc::dev_free(dpts, s);  // the octree holds its own copy
+    sfc_status st = octree_build(dpts, r.n_points, S->o.enc, &o, s, &q.tree);  // copies what it keeps
     if (st != SFC_OK) return st;
     q.rows = r.queries_xyz ? r.n_queries : r.n_points;
     if (r.queries_xyz) {
-        SFC_TRY(sfc::dev_alloc(&dq, 3 * r.n_queries, s));
+        SFC_TRY(scratch.alloc(&dq, 3 * r.n_queries));
         if (r.n_queries > 0)
             SFC_CUDA(cudaMemcpyAsync(dq, r.queries_xyz, sizeof(float) * 3 * r.n_queries, cudaMemcpyHostToDevice, s));
     }
@@ -130,7 +130,6 @@ sfc_status run_single(sfc_server_s* S, Request& q, cudaStream_t s) {
         if (st == SFC_OK) st = sfc::dev_alloc(&q.knn_d2, q.rows * r.k, s);
         if (st == SFC_OK) st = knn(q.tree, dq, r.queries_xyz ? r.n_queries : 0, r.k, s, q.knn_idx, q.knn_d2);
     }
-    sfc::dev_free(dq, s);
     if (st != SFC_OK) return st;
     SFC_CUDA(cudaStreamSynchronize(s));
     return SFC_OK;
@@ -151,7 +150,8 @@ sfc_status run_merged(sfc_server_s* S, std::vector<Request*>& group, cudaStream_
         total += r.n_points;
     }
     float* dpts = nullptr;
-    SFC_TRY(sfc::dev_alloc(&dpts, 3 * total, s));
+    sfc::Scratch scratch(s);  // the device copy of the clouds, freed in stream order on return
+    SFC_TRY(scratch.alloc(&dpts, 3 * total));
     int64_t off = 0;
     for (Request* q : group) {
         if (q->req.n_points > 0)
@@ -166,7 +166,6 @@ sfc_status run_merged(sfc_server_s* S, std::vector<Request*>& group, cudaStream_
     pass->stream = s;
     const sfc_status st = batch_search(dpts, clouds.data(), static_cast<int32_t>(clouds.size()), S->o.enc, &o, s,
                                        &pass->batch);
-    sfc::dev_free(dpts, s);
     if (st != SFC_OK) return st;
     for (size_t i = 0; i < group.size(); ++i) {
         Request& q = *group[i];
