@@ -3,6 +3,7 @@ ALU side computed from the work counters."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -35,3 +36,21 @@ def test_every_search_kind_has_an_operation_count():
     # kernels drop the z product or use maxima
     assert bench.FP32_OPS_PER_TEST["sphere"] == bench.FP32_OPS_PER_TEST["knn"] == 9
     assert bench.FP32_OPS_PER_TEST["square"] < bench.FP32_OPS_PER_TEST["circle"] < 9
+
+
+def test_serving_trace_follows_its_recipe():
+    """Poisson arrivals at the given rate, clouds drawn log-uniformly over the pool, half
+    all-points and half 1 % subsets, half sphere and half kNN; seeded."""
+    pool = [int(round(x)) for x in np.exp(np.linspace(np.log(50_000), np.log(20_000_000), 16))]
+    trace = bench.serve_trace(10.0, 200.0, pool, 77)
+    n = len(trace)
+    assert abs(n - 2000) < 5 * 2000 ** 0.5  # Poisson count within five standard deviations
+    t = [rq["t"] for rq in trace]
+    assert t == sorted(t) and 0.0 <= t[0] and t[-1] < 10.0
+    assert all(0 <= rq["cloud"] < len(pool) for rq in trace)
+    assert 0.45 < sum(rq["subset"] for rq in trace) / n < 0.55
+    radius = [rq for rq in trace if rq["search"] == "radius"]
+    assert 0.45 < len(radius) / n < 0.55
+    assert all(rq["kernel"] == "sphere" and rq["r"] in (0.5, 1.0, 2.0, 3.0) for rq in radius)
+    assert all(rq["k"] in (8, 16, 32) for rq in trace if rq["search"] == "knn")
+    assert bench.serve_trace(10.0, 200.0, pool, 77) == trace

@@ -35,3 +35,35 @@ def test_lidar_tile_shape():
 def test_gaussian_clusters_shape():
     xyz = synth.gaussian_clusters(50_000, 3)
     assert xyz.shape == (50_000, 3) and np.isfinite(xyz).all()
+
+
+def test_batch_workload_matches_its_recipe():
+    """The 256-cloud batch: log-uniform sizes on [10k, 2M] (95.4M points in all), the three
+    generators in turn, about half radius (r from the set) and half kNN (k from the set)."""
+    specs = synth.batch_workload()
+    assert len(specs) == 256
+    sizes = np.array([s["n"] for s in specs])
+    assert sizes.min() >= 10_000 and sizes.max() <= 2_000_000
+    assert sizes.sum() == 95_396_245
+    # log-uniform: the median of log(n) sits near the middle of [log 10k, log 2M]
+    mid = 0.5 * (np.log(10_000) + np.log(2_000_000))
+    assert abs(np.median(np.log(sizes)) - mid) < 0.5
+    assert [s["gen"] for s in specs[:6]] == list(synth.BATCH_GENERATORS) * 2
+    radius = [s for s in specs if s["search"] == "radius"]
+    knn = [s for s in specs if s["search"] == "knn"]
+    assert len(radius) + len(knn) == 256 and 100 < len(radius) < 156
+    assert {s["r"] for s in radius} <= set(synth.BATCH_RADII) and {s["k"] for s in knn} <= set(synth.BATCH_KS)
+    assert synth.batch_workload() == specs  # seeded
+
+
+def test_batch_cloud_scales():
+    """Uniform cubes at 2 pts/m^3, LiDAR tiles at 10 pts/m^2."""
+    spec = dict(gen="uniform", n=20_000, seed=5)
+    xyz = synth.batch_cloud(spec)
+    side = (20_000 / 2.0) ** (1.0 / 3.0)
+    assert xyz.shape == (20_000, 3) and xyz.min() >= 0.0 and xyz.max() < side
+    tile = synth.batch_cloud(dict(gen="lidar", n=20_000, seed=6))
+    side = np.sqrt(20_000 / 10.0)  # the ground covers the tile; crowns and roofs may overhang it
+    on_tile = np.all((tile[:, :2] >= -0.2) & (tile[:, :2] < side + 0.2), axis=1)
+    assert on_tile.mean() > 0.85
+    assert synth.batch_cloud(dict(gen="clusters", n=0, seed=1)).shape == (0, 3)
