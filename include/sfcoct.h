@@ -178,6 +178,8 @@ typedef struct {
  * output (release with sfc_ranges_free); synchronises cuda_stream as radius_search. */
 sfc_status radius_search_ranges(sfc_octree h, const float* queries_xyz, int64_t n_queries, float r, sfc_kernel kern,
                                 void* cuda_stream, sfc_ranges* out);
+/* Free (in stream order on cuda_stream) the two arrays of a range output and clear *ranges;
+ * SFC_ERR_INVALID for ranges == NULL. */
 sfc_status sfc_ranges_free(sfc_ranges* ranges, void* cuda_stream);
 
 /* k nearest neighbours (section 3.3) under the squared Euclidean distance in binary32,
@@ -395,6 +397,8 @@ sfc_status server_result(sfc_server s, int64_t id, sfc_request_result* out);
 /* Free a finished request's octree and results (its memory leaves the budget). */
 sfc_status server_release(sfc_server s, int64_t id);
 
+/* A snapshot of the server's counters (host struct, no device synchronisation);
+ * SFC_ERR_INVALID for a NULL server or out. */
 sfc_status server_stats(sfc_server s, sfc_server_stats* out);
 
 /* Finish the queued requests, stop the workers and free everything. */
