@@ -54,3 +54,30 @@ def test_serving_trace_follows_its_recipe():
     assert all(rq["kernel"] == "sphere" and rq["r"] in (0.5, 1.0, 2.0, 3.0) for rq in radius)
     assert all(rq["k"] in (8, 16, 32) for rq in trace if rq["search"] == "knn")
     assert bench.serve_trace(10.0, 200.0, pool, 77) == trace
+
+
+def _profile_rows(name: str) -> dict:
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles", name)
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 4 and cells[0].startswith("k_"):
+                rows.setdefault(cells[0], []).append(cells[1:])
+    return rows
+
+
+def test_roofline_counters_match_the_committed_profile():
+    """The DRAM traffic and instruction counts the bench line carries are the ones the
+    committed ncu summary reports."""
+    rows = _profile_rows("traffic_search_kernels_lidar_tile_10M.md")
+    gb = lambda s: float(s.split()[0]) * 1e9  # noqa: E731
+    traffic = {"knn": rows["k_knn_group<16>"][0], "radius_count": rows["k_radius_group count (records on)"][0],
+               "radius_fill": rows["k_radius_group fill (replay)"][0]}
+    for kernel, cells in traffic.items():
+        assert bench.NCU_TRAFFIC[kernel]["bytes_per_launch"] == pytest.approx(gb(cells[1]) + gb(cells[2]), rel=0.01)
+    inst = {"knn": rows["k_knn_group<16>"][1], "radius_count": rows["k_radius_group count"][0],
+            "radius_fill": rows["k_radius_group fill"][0]}
+    for kernel, cells in inst.items():
+        per_group = float(cells[1].split()[0]) * 1e6 / 62500
+        assert bench.NCU_INST_PER_GROUP[kernel]["warp_inst"] == pytest.approx(per_group, rel=0.01)
