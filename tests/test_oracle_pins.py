@@ -176,6 +176,35 @@ def test_leaves_invariants_and_pointer_octree(gen, n, ncap):
         assert np.array_equal(nd["count"][nd["is_leaf"] == 1], p.counts[lidx])
 
 
+@pytest.mark.parametrize("gen", ["uniform", "lidar", "dup"])
+def test_node_boxes_are_the_tight_boxes(gen):
+    """Every node's box is the min/max of its own points, no larger and no smaller (the
+    pruning boxes of reading 8): the points of the node at (first code, level) are those
+    whose code lies in [first, first + 8^(21 - level)) (section 5.1), here found with numpy
+    over the sorted codes; empty nodes carry the empty box (+inf, -inf)."""
+    xyz = {"uniform": lambda: synth.uniform_cube(4000, 12),
+           "lidar": lambda: synth.lidar_tile(5000, 13, side=25.0),
+           "dup": lambda: np.repeat(synth.uniform_cube(200, 14), 20, axis=0)}[gen]()
+    for enc in (oracle.ENC_MORTON, oracle.ENC_HILBERT):
+        p = oracle.Pipeline(xyz, enc, 16)
+        nd = p.nodes()
+        sk = p.sorted_keys
+        pts = xyz[p.perm.astype(np.int64)]
+        for i in range(len(nd["key"])):
+            first = int(nd["key"][i])
+            span = 1 << (3 * (oracle.L - int(nd["level"][i])))
+            a = int(np.searchsorted(sk, np.uint64(first), "left"))
+            b = int(np.searchsorted(sk, np.uint64(first + span - 1), "right"))
+            assert nd["count"][i] == b - a
+            box = nd["box"][i]
+            if b == a:
+                assert np.isposinf(box[:3]).all() and np.isneginf(box[3:]).all()
+                continue
+            assert (nd["start"][i], nd["end"][i]) == (a, b)
+            assert np.array_equal(box[:3], pts[a:b].min(0)), (gen, enc, i)
+            assert np.array_equal(box[3:], pts[a:b].max(0)), (gen, enc, i)
+
+
 def test_leaves_closed_forms():
     # N <= N_max: the root is the only leaf
     lv, ct = oracle.leaves(np.arange(10, dtype=np.uint64), 32)
@@ -263,6 +292,60 @@ def test_boundary_report_runs():
     assert oracle.boundary_disagreements(xyz, xyz, r, oracle.SPHERE) == 0
 
 
+def _rounding_cases():
+    """Rows of rounding_cases.txt grouped by kernel: (points, centre, r, columns)."""
+    groups = {}
+    for row in read_golden("rounding_cases.txt"):
+        vals = [np.float32(float.fromhex(v)) for v in row[1:8]]
+        cols = {name: (None if v == "-" else bool(int(v)))
+                for name, v in zip(("inside", "o2", "o3", "fma1", "fma2", "f64"), row[8:14])}
+        g = groups.setdefault(row[0], dict(p=[], c=vals[3:6], r=vals[6], cols=[]))
+        assert g["c"] == vals[3:6] and g["r"] == vals[6]          # one centre and radius per kernel
+        g["p"].append(vals[0:3])
+        g["cols"].append(cols)
+    return groups
+
+
+def test_kernel_rounding_cases():
+    """Section 3.2 tests at the rounding boundary, decided by exact rational arithmetic
+    (tests/golden/make_rounding_cases.py): the oracle takes the reading's decision on every
+    row, and every plausible mistake (another summation order, a fused multiply-add, the
+    test evaluated in binary64) takes another one on at least one row."""
+    groups = _rounding_cases()
+    assert set(groups) == set(KNAME)
+    for name, g in groups.items():
+        kern = KNAME[name]
+        c = np.array(g["c"], np.float32)
+        for p, cols in zip(g["p"], g["cols"]):
+            assert oracle.pred(kern, np.array(p, np.float32), c, float(g["r"])) == cols["inside"], (name, p)
+        for alt in ("o2", "o3", "fma1", "fma2", "f64"):
+            if any(cols[alt] is not None for cols in g["cols"]):
+                assert any(cols[alt] != cols["inside"] for cols in g["cols"]), (name, alt)
+        # the searches decide the same: brute force and the pointer octree
+        xyz = np.array(g["p"], np.float32)
+        want = [i for i, cols in enumerate(g["cols"]) if cols["inside"]]
+        rp, got = oracle.radius_brute(xyz, c[None], float(g["r"]), kern)
+        assert got.tolist() == want
+        rp, got = oracle.PointerOctree(xyz, 2).radius(c[None], float(g["r"]), kern)
+        assert got.tolist() == want
+
+
+def test_boundary_report_counts_the_disagreements():
+    """The boundary report counts the (point, centre) pairs whose binary32 decision differs
+    from the binary64 evaluation of the same expression; the rounding cases fix the count."""
+    total = 0
+    for name, g in _rounding_cases().items():
+        want = sum(cols["inside"] != cols["f64"] for cols in g["cols"])
+        assert want > 0
+        xyz = np.array(g["p"], np.float32)
+        c = np.array(g["c"], np.float32)[None]
+        assert oracle.boundary_disagreements(xyz, c, float(g["r"]), KNAME[name]) == want, name
+        # every pair counted once: the same centre twice doubles the count
+        assert oracle.boundary_disagreements(xyz, np.repeat(c, 2, 0), float(g["r"]), KNAME[name]) == 2 * want
+        total += want
+    assert total >= 16
+
+
 # ----------------------------------------------------------------------------- section 3.3 kNN
 def test_knn_hand_example():
     xyz = np.array([[i, 0, 0] for i in range(10)], np.float32)
@@ -271,6 +354,33 @@ def test_knn_hand_example():
     assert d2.tolist() == [[0.25, 0.25, 2.25, 2.25, 6.25]]
     idx, d2 = oracle.knn_brute(xyz[:3], np.array([[0, 0, 0]], np.float32), 5)
     assert idx.tolist() == [[0, 1, 2, -1, -1]] and np.isinf(d2[0, 3:]).all()
+
+
+def test_knn_rounding_order():
+    """Section 3.3 order of two candidates whose binary32 squared distances tie or differ by
+    one unit in the last place (tests/golden/knn_rounding_cases.txt, exact rational
+    arithmetic): the oracle's distances are the reading's bit for bit and its order puts the
+    smaller first, a tie to the smaller index; another summation order or a fused
+    multiply-add flips the order on at least one row."""
+    rows = read_golden("knn_rounding_cases.txt")
+    flips = {k: 0 for k in ("o2", "o3", "fma1", "fma2")}
+    ties = 0
+    for row in rows:
+        f = [np.float32(float.fromhex(v)) for v in row[0:9]]
+        c, p0, p1 = np.array(f[0:3])[None], f[3:6], f[6:9]
+        order, d0, d1 = row[9], np.float32(float.fromhex(row[10])), np.float32(float.fromhex(row[11]))
+        ties += d0 == d1
+        for k, v in zip(flips, row[12:16]):
+            flips[k] += v != order
+        want = [0, 1] if order == "01" else [1, 0]
+        xyz = np.array([p0, p1], np.float32)
+        for idx, d2 in (oracle.knn_brute(xyz, c, 2), oracle.PointerOctree(xyz, 1).knn(c, 2)):
+            assert idx[0].tolist() == want, row
+            assert d2[0].tobytes() == np.array([d0, d1][::1 if want == [0, 1] else -1], np.float32).tobytes()
+        # the same two points in the other storage order: a tie now goes to the other one
+        idx, _ = oracle.knn_brute(xyz[::-1].copy(), c, 1)
+        assert idx[0, 0] == (0 if (d1 < d0 or d0 == d1) else 1), row
+    assert ties >= 2 and all(v > 0 for v in flips.values()), (ties, flips)
 
 
 @pytest.mark.parametrize("name", ["uniform", "lattice", "dup", "lidar", "flat"])
@@ -372,16 +482,19 @@ def test_locality_histogram_properties():
     assert (h * d).sum() < (h_none * d).sum()
 
 
-def test_skewness_matches_library_and_closed_forms():
-    """G1 of section 5.2 against scipy's biased sample skewness on the expanded sample,
-    a symmetric histogram (0) and the two-point (Bernoulli) closed form
-    (1 - 2q) / sqrt(q (1 - q)), q the share at d = 1."""
+def test_skewness_matches_library():
+    """G1 of section 5.2 against scipy's biased sample skewness on the expanded sample."""
     stats = pytest.importorskip("scipy.stats")
     rng = synth.Rng(71)
     for t in range(4):
         h = rng.integers(t, 60, 50).astype(np.int64)
         d = np.repeat(np.arange(len(h)), h)
         assert abs(oracle.skewness(h) - stats.skew(d, bias=True)) < 1e-9
+
+
+def test_skewness_closed_forms():
+    """G1 of section 5.2 on a symmetric histogram (0), the two-point (Bernoulli) closed form
+    (1 - 2q) / sqrt(q (1 - q)), q the share at d = 1, and a point mass (0); no library."""
     assert abs(oracle.skewness([1, 4, 6, 4, 1])) < 1e-12
     for a, b in ((1, 3), (2, 7), (5, 1)):
         q = b / (a + b)
