@@ -186,16 +186,22 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- the step
-def run_step(sfc, pts, cfg):
+def run_step(sfc, pts, cfg, sphere_events=None):
     """The whole path once; returns (tree, row_ptr, cols, nnz, idx, d2).  With the range
-    output, (row_ptr, cols, nnz) are the run pointers, the runs and their number."""
+    output, (row_ptr, cols, nnz) are the run pointers, the runs and their number.
+    sphere_events: a pair of CUDA events recorded around the radius search (count, scan
+    and fill) on the current stream."""
     tree = sfc.octree_build(pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
+    if sphere_events is not None:
+        sphere_events[0].record()
     if cfg["radius"].get("output") == "ranges":
         row_ptr, cols = sfc.radius_search_ranges(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
         nnz = int(cols.shape[0])
     else:
         row_ptr, nnz = sfc.radius_count(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"])
         cols = sfc.radius_fill(tree, None, cfg["radius"]["r"], cfg["radius"]["kernel"], row_ptr, nnz)
+    if sphere_events is not None:
+        sphere_events[1].record()
     idx, d2 = sfc.knn(tree, None, cfg["knn_k"])
     return tree, row_ptr, cols, nnz, idx, d2
 
@@ -258,30 +264,6 @@ def load_peaks() -> tuple[float, str]:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def time_oracle(xyz: np.ndarray, cfg: dict, sample: int, seed: int, build_s: float | None = None):
-    """Oracle timing: a full build (section 4 + 5.1 + pointer octree) unless build_s is
-    given, then radius + kNN on a seeded sample of centres; returns seconds."""
-    import oracle
-
-    enc = oracle.ENCODINGS[cfg["encoding"]]
-    if build_s is None:
-        t0 = time.perf_counter()
-        pipe = oracle.Pipeline(xyz, enc, cfg["leaf_capacity"])
-        build_s = time.perf_counter() - t0
-    else:
-        pipe = time_oracle.pipe
-    time_oracle.pipe = pipe
-    rows = np.sort(np.random.default_rng(seed).choice(len(xyz), sample, replace=False))
-    q = xyz[rows]
-    t0 = time.perf_counter()
-    pipe.tree.radius(q, cfg["radius"]["r"], oracle.KERNELS[cfg["radius"]["kernel"]])
-    radius_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    pipe.tree.knn(q, cfg["knn_k"])
-    knn_s = time.perf_counter() - t0
-    return build_s, radius_s, knn_s
-
-
 def cpu_model() -> str:
     """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
     try:
@@ -301,41 +283,69 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def cpu_step_estimate(n: int, sample: int, build_s: float, radius_s: float, knn_s: float) -> float:
-    """Seconds of one full step on the CPU: the build plus the sampled searches scaled to n centres."""
-    return build_s + (radius_s + knn_s) * n / sample
+# The oracle's step: the same workload on a smaller tile of the same generator (same
+# density and structure, side sqrt(n / 10) m), the whole path measured: build, all-points
+# sphere search, all-points kNN.  Nothing is scaled or extrapolated.
+ORACLE_TILE_POINTS = 200_000
+
+
+def oracle_step(xyz: np.ndarray, cfg: dict) -> tuple[float, float, float]:
+    """One full oracle step over ``xyz``: seconds of the build, the radius and the kNN search."""
+    import oracle
+
+    enc = oracle.ENCODINGS[cfg["encoding"]]
+    t0 = time.perf_counter()
+    pipe = oracle.Pipeline(xyz, enc, cfg["leaf_capacity"])
+    t1 = time.perf_counter()
+    pipe.tree.radius(xyz, cfg["radius"]["r"], oracle.KERNELS[cfg["radius"]["kernel"]])
+    t2 = time.perf_counter()
+    pipe.tree.knn(xyz, cfg["knn_k"])
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2
+
+
+def oracle_tile(n: int, step: int) -> np.ndarray:
+    """The oracle's bounded sample: a LiDAR-like tile of min(n, ORACLE_TILE_POINTS) points
+    (seeded per step)."""
+    import synth
+
+    return synth.lidar_tile(min(n, ORACLE_TILE_POINTS), synth.CONFIG_SEED[2] + 7919 * (step + 1))
+
+
+def bench_config(cfg: dict, n: int, world: int) -> dict:
+    """The ``config`` object of both arms' lines (identical keys and values)."""
+    return dict(cfg, points=n, l2="flushed before every timed step (512 MiB write)",
+                parallelism="replicas" if world > 1 else "single GPU")
 
 
 def reference_arm(args, cfg):
     import oracle
-    import synth
 
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     n = args.points
-    xyz = synth.lidar_tile(n, synth.CONFIG_SEED[2]) if n != WORKLOAD["points"] else synth.config_cloud(2)
     cores = oracle.num_cpus()
-    sample = max(1, min(n, 4000))
-    build_s, _, _ = time_oracle(xyz, cfg, sample, 0)          # the build, timed once
+    m = min(n, ORACLE_TILE_POINTS)
     for w in range(args.warmup):
-        time_oracle(xyz, cfg, sample, 1000 + w, build_s)
-    steps = []
+        oracle_step(oracle_tile(n, 1000 + w), cfg)
+    parts = []
     for s in range(args.steps):
-        _, rs, ks = time_oracle(xyz, cfg, sample, s, build_s)
-        steps.append(cpu_step_estimate(n, sample, build_s, rs, ks))
-    step_s = statistics.mean(steps)
-    value = 2 * n / step_s
+        parts.append(oracle_step(oracle_tile(n, s), cfg))
+    step_s = statistics.mean(sum(p) for p in parts)
+    value = 2 * m / step_s
+    mb, mr, mk = (statistics.mean(p[i] for p in parts) for i in range(3))
+    sample = (f"each step: the whole path of the oracle (plain C; pointer octree; build on 1 thread, "
+              f"searches on {cores} threads) on a {m}-point LiDAR-like tile of the same generator and "
+              f"density (its own seed per step): build {mb:.3f} s + all-points sphere r={cfg['radius']['r']} "
+              f"{mr:.3f} s + all-points kNN k={cfg['knn_k']} {mk:.3f} s; value = {2 * m} queries / measured "
+              f"step time; nothing extrapolated")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(cfg, points=n),
-        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
-                         "sample": (f"oracle (plain C pointer octree, {cores} threads for searches, 1 thread for "
-                                    f"the build) on the same {n}-point cloud: full build timed once "
-                                    f"({build_s:.2f} s); each step times sphere r=2 and kNN k=16 on {sample} "
-                                    f"seeded centres and scales them to all {n} centres")},
+        "config": bench_config(cfg, n, world),
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -798,6 +808,8 @@ def main(argv=None):
                           if args.clocks_csv else None)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sphere_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -809,7 +821,7 @@ def main(argv=None):
     for s in range(args.steps):
         flush.fill_(s)
         starts[s].record(stream)
-        tree, row_ptr, cols, nnz, idx, d2 = run_step(sfc, pts, cfg)
+        tree, row_ptr, cols, nnz, idx, d2 = run_step(sfc, pts, cfg, sphere_ev[s])
         ends[s].record(stream)
         tree.free()
         del row_ptr, cols, idx, d2
@@ -856,6 +868,29 @@ def main(argv=None):
                                        "peak = 152 SMs x 4 sub-partitions x median SM clock"}
     kernels = {name: {"launches": c, "total_ms": ms, "share": ms / sum(step_ms)} for name, (c, ms) in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # the fixed-radius search as one unit (count, scan of the counts, host read of the total,
+    # fill), timed by CUDA events around the two calls in every timed step
+    sphere_ms = statistics.mean(a.elapsed_time(b) for a, b in sphere_ev)
+    roof_sphere = None
+    out_kind = "radius_ranges_fill" if cfg["radius"].get("output") == "ranges" else "radius_fill"
+    sph_alg = algorithmic_bytes(out_kind, n, nnz, k)
+    if sph_alg is not None:
+        sph_ach = sph_alg / (sphere_ms / 1e3) / 1e9
+        tr = [NCU_TRAFFIC.get(x) for x in ("radius_count", "radius_fill")]
+        sph_traffic = (sum(t["bytes_per_launch"] for t in tr)
+                       if all(t and t.get("sha256") == source_sha("sfc_radius.cu") for t in tr) else None)
+        roof_sphere = {"bound": "hbm", "search": f"{cfg['radius']['kernel']} r={cfg['radius']['r']} all points",
+                       "achieved": sph_ach, "peak": peak, "unit": "GB/s", "frac": sph_ach / peak,
+                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                       else "fallback 6.8 TB/s", "traffic": sph_traffic, "algorithmic_bytes": sph_alg,
+                       "ms": sphere_ms,
+                       "kernels_ms": {x: prof[x][1] / prof[x][0] for x in ("radius_count", "radius_fill",
+                                                                            "radius_ranges_count",
+                                                                            "radius_ranges_fill") if x in prof},
+                       "note": "count + scan + fill as one unit: algorithmic bytes 16 N (points and ids) + "
+                               "8 (N + 1) (row pointers) + 4 nnz (neighbour ids) over the CUDA-event time "
+                               "between the start of the count and the end of the fill"}
 
     # candidate tests of the two search kernels (instrumented copies, run once, untimed)
     tests = {}
@@ -926,37 +961,33 @@ def main(argv=None):
     if rank == 0 and world >= 1 and not args.no_cpu_baseline and args.gpus == 1:
         import oracle
 
-        sample = min(n, 20000)
-        b_s, r_s, k_s = time_oracle(xyz, cfg, sample, 7)
-        est = cpu_step_estimate(n, sample, b_s, r_s, k_s)
-        # one thread, on a tenth of the sample
-        rows1 = np.sort(np.random.default_rng(8).choice(n, max(1, sample // 10), replace=False))
-        t0 = time.perf_counter()
-        time_oracle.pipe.tree.radius(xyz[rows1], cfg["radius"]["r"], oracle.KERNELS[cfg["radius"]["kernel"]], 1)
-        time_oracle.pipe.tree.knn(xyz[rows1], cfg["knn_k"], 1)
-        one_s = (time.perf_counter() - t0) * n / len(rows1) + b_s
-        # binary32 decisions that binary64 would take the other way (a brute-force scan, so
-        # on 2000 of the sampled centres)
+        m = min(n, ORACLE_TILE_POINTS)
+        parts = [oracle_step(oracle_tile(n, s), cfg) for s in range(3)]
+        step_s = statistics.mean(sum(p) for p in parts)
+        mb, mr, mk = (statistics.mean(p[i] for p in parts) for i in range(3))
+        # binary32 decisions that binary64 would take the other way (a brute-force scan over
+        # the benchmark's own cloud, so for 2000 seeded centres)
         rows_b = np.sort(np.random.default_rng(7).choice(n, min(n, 2000), replace=False))
         boundary = oracle.boundary_disagreements(xyz, xyz[rows_b], cfg["radius"]["r"],
                                                  oracle.KERNELS[cfg["radius"]["kernel"]])
-        cpu = {"value": 2 * n / est, "unit": UNIT, "cores": oracle.num_cpus(), "kind": "oracle",
-               "cpu_model": cpu_model(), "single_thread_value": 2 * n / one_s,
+        cpu = {"value": 2 * m / step_s, "unit": UNIT, "cores": oracle.num_cpus(), "kind": "oracle",
+               "cpu_model": cpu_model(),
                "boundary_disagreements": {"centres": len(rows_b), "pairs_decided_differently_in_binary64": boundary},
-               "sample": (f"full oracle build of the {n}-point cloud ({b_s:.2f} s, 1 thread) + sphere r=2 "
-                          f"({r_s:.3f} s) and kNN k=16 ({k_s:.3f} s) for {sample} seeded centres on "
-                          f"{oracle.num_cpus()} threads, scaled to {n} centres; single_thread_value: the "
-                          f"same searches on {len(rows1)} centres on one thread")}
+               "sample": (f"3 steps of the oracle's whole path (plain C; build on 1 thread, searches on "
+                          f"{oracle.num_cpus()} threads) on {m}-point LiDAR-like tiles of the same generator "
+                          f"and density: build {mb:.3f} s + all-points sphere r={cfg['radius']['r']} {mr:.3f} s "
+                          f"+ all-points kNN k={cfg['knn_k']} {mk:.3f} s per step; value = {2 * m} queries / "
+                          f"measured step time")}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(cfg, points=n, l2="flushed before every timed step (512 MiB write)",
-                           parallelism="replicas" if world > 1 else "single GPU"),
+            "config": bench_config(cfg, n, world),
             "nnz": nnz, "mu": nnz / n, "neighbours_per_s": nnz * args.steps * world / (total_ms / 1e3),
-            "gpu_launches": launches, "wall_s": wall_s, "roofline": roof, "kernels": kernels,
+            "gpu_launches": launches, "wall_s": wall_s, "roofline": roof, "roofline_sphere": roof_sphere,
+            "kernels": kernels,
             "candidate_tests": tests, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

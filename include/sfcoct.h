@@ -354,11 +354,11 @@ typedef struct {
 } sfc_request;
 
 typedef struct {
-    const int64_t* row_ptr;   /* radius: device, n_rows + 1 entries; row i is
-                                 cols[row_ptr[i] - row_base .. row_ptr[i + 1] - row_base) */
+    const int64_t* row_ptr;   /* radius: device, n_rows + 1 entries, row_ptr[0] == 0; row i is
+                                 cols[row_ptr[i] .. row_ptr[i + 1]) */
     const int32_t* cols;      /* radius: device, nnz entries (ids are positions in the cloud) */
     int64_t nnz;
-    int64_t row_base;
+    int64_t row_base;         /* always 0 (kept for the layout) */
     const int32_t* knn_idx;   /* kNN: device, n_rows x k (layout of knn()) */
     const float* knn_d2;
     int64_t n_rows;
@@ -401,7 +401,8 @@ sfc_status server_release(sfc_server s, int64_t id);
  * SFC_ERR_INVALID for a NULL server or out. */
 sfc_status server_stats(sfc_server s, sfc_server_stats* out);
 
-/* Finish the queued requests, stop the workers and free everything. */
+/* Stop accepting requests, free the results of finished ones, run the queued requests to
+ * the end (still admitted within the memory budget), stop the workers and free everything. */
 sfc_status server_destroy(sfc_server s);
 
 /* ---- device memory ---------------------------------------------------------------- */

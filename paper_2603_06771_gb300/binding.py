@@ -677,7 +677,7 @@ class Server:
         n = res.n_rows
         if search == "radius":
             rp = torch.as_tensor(_DeviceArray(self, res.row_ptr, n + 1, "<i8"), device="cuda").clone()
-            out["row_ptr"] = rp - res.row_base
+            out["row_ptr"] = rp
             out["cols"] = (torch.as_tensor(_DeviceArray(self, res.cols, res.nnz, "<i4"), device="cuda").clone()
                            if res.nnz else torch.empty(0, dtype=torch.int32, device="cuda"))
         else:

@@ -81,3 +81,19 @@ def test_roofline_counters_match_the_committed_profile():
     for kernel, cells in inst.items():
         per_group = float(cells[1].split()[0]) * 1e6 / 62500
         assert bench.NCU_INST_PER_GROUP[kernel]["warp_inst"] == pytest.approx(per_group, rel=0.01)
+
+
+def test_reference_arm_line_is_measured_and_shares_the_config(capsys, monkeypatch):
+    """The reference arm times whole oracle steps (no extrapolation): ms_per_step is the
+    measured mean step and value = queries of one step / that time; its config object is
+    the GPU arm's, key for key."""
+    monkeypatch.setattr(bench, "ORACLE_TILE_POINTS", 3000)
+    assert bench.main(["--impl", "reference", "--points", "5000", "--steps", "2", "--warmup", "1"]) == 0
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] == pytest.approx(2 * 3000 / (line["ms_per_step"] / 1e3))
+    assert "extrapolat" not in json.dumps(line) or "nothing extrapolated" in line["cpu_baseline"]["sample"]
+    cfg = dict(bench.WORKLOAD, radius={"kernel": "sphere", "r": 2.0})
+    assert line["config"] == json.loads(json.dumps(bench.bench_config(cfg, 5000, 1)))
+    assert line["cpu_baseline"]["value"] == line["value"] and line["e2e"]["value"] == line["value"]
