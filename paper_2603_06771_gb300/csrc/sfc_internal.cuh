@@ -61,6 +61,7 @@ struct RadiusRecords {
 };
 constexpr uint32_t kRecordsOverflow = 0xffffffffu;
 constexpr int kRecordCap = 32;  // record slots per warp of 32 centres (more: the fill walks again)
+constexpr int kRecordCapSingle = 64;  // the same for the search of one cloud
 
 // The records of one batched radius launch: [groups][kRecordCap] slots (null: no records)
 struct BatchRecords {
