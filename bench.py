@@ -417,7 +417,8 @@ def batch_main(args):
     clouds = [dict(n=sp["n"], search=sp["search"], kernel=sp.get("kernel", "sphere"), r=sp.get("r", 0.0),
                    k=sp.get("k", 0)) for sp in specs]
     tune_s = None
-    if not args.no_tune:  # per-cloud leaf capacity and kNN seeding window from the device autotuner
+    if not args.no_tune:  # per-cloud leaf capacity, kNN seeding window, centres per warp walk and
+        # record slots from the device autotuner
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         clouds = sfc.batch_autotune(pts, clouds, enc, leaf_capacity=ncap)
@@ -493,6 +494,9 @@ def batch_main(args):
                        "leaf_capacity_chosen": sorted({int(c.get("leaf_capacity") or ncap) for c in clouds}),
                        "knn_window_chosen": sorted({int(c.get("knn_window", 0)) for c in clouds
                                                     if c["search"] == "knn"}),
+                       "queries_per_warp_chosen": sorted({int(c.get("queries_per_warp") or 32) for c in clouds}),
+                       "record_slots_chosen": sorted({int(c.get("record_slots") or 32) for c in clouds
+                                                      if c["search"] == "radius"}),
                        "nnz": int(sum(sp.get("nnz", 0) for sp in specs)),
                        "l2": "flushed before every timed step (512 MiB write)"},
             "plain": {"value": units / (p_total / 1e3), "ms_per_step": p_total / args.steps},

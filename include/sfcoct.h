@@ -210,6 +210,14 @@ typedef struct {
     int32_t knn_window;    /* SFC_SEARCH_KNN: curve neighbours per side that seed each list,
                               0..64 (0 = max(8, k), the default of knn()); a speed knob only
                               (a window wider than the list size class allows is not used) */
+    int32_t queries_per_warp; /* centres one warp walks the octree for together: 8, 16 or 32
+                                 (0 = 32); fewer centres give each walk a tighter box but
+                                 leave lanes idle; a speed knob only */
+    int32_t record_slots;  /* SFC_SEARCH_RADIUS: hit-mask records kept per warp group from the
+                              count pass for the fill (the staging depth of the two passes),
+                              1..128 (0 = 32); a group with more leaf chunks than slots walks
+                              the tree again in the fill.  Clouds of one kernel type share the
+                              largest value among them.  A speed and memory knob only */
 } sfc_batch_cloud;
 
 typedef struct sfc_batch_s* sfc_batch; /* results of a batch, owned by the library */
@@ -246,20 +254,27 @@ sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_pt
 /* Release a batch's results (stream ordered on cuda_stream). */
 sfc_status batch_free(sfc_batch b, void* cuda_stream);
 
-/* Choose every cloud's leaf capacity and (kNN) seeding window for this batch by timing it:
- * one pass per candidate leaf capacity (after one untimed warm pass), the build timed whole
- * and every launch set (radius kernel type: count + fill; kNN list size 8/16/32/64) on its
- * own with CUDA events; each set takes the capacity minimising its search time plus its
- * points' share of the build time.  Then one pass per candidate window at those
- * capacities picks each kNN set's window.  Writes leaf_capacity_out[n_clouds] and
- * knn_window_out[n_clouds] (0 for radius clouds), ready for sfc_batch_cloud.  Results of a
- * batch do not depend on either knob.  The paper has no counterpart (it fixes N_max per
- * run).  Errors as batch_search, plus SFC_ERR_INVALID for a candidate < 1 or a window
- * above 64.  Synchronises cuda_stream repeatedly. */
+/* Choose every cloud's speed knobs for this batch by timing it on the device: leaf
+ * capacity, seeding window (kNN), centres per warp walk and record slots (radius).  The
+ * build is timed whole and every launch set (radius kernel type: count + fill; kNN list
+ * size 8/16/32/64) on its own with CUDA events.  First one pass per candidate leaf
+ * capacity (after one untimed warm pass): each set takes the capacity minimising its
+ * search time plus its points' share of the build time.  Then, at those capacities, one
+ * pass per candidate window picks each kNN set's window, one pass per candidate
+ * centres-per-warp value picks each set's, and one pass per candidate record-slot count
+ * picks each radius set's.  An empty candidate list keeps the cloud's own value (or the
+ * default).  Writes tuned_out[n_clouds]: the clouds with the chosen leaf_capacity,
+ * knn_window (0 for radius clouds), queries_per_warp and record_slots (0 for kNN clouds),
+ * ready for batch_search.  Results of a batch depend on none of these knobs.  The paper has
+ * no counterpart (it fixes N_max per run and serves one centre per thread).  Errors as
+ * batch_search, plus SFC_ERR_INVALID for a leaf candidate < 1, a window outside 1..64, a
+ * centres-per-warp value other than 8, 16 or 32, or a record-slot count outside 1..128.
+ * Synchronises cuda_stream repeatedly. */
 sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
                           const sfc_build_opts* opts, const int32_t* leaf_candidates, int32_t n_leaf,
-                          const int32_t* window_candidates, int32_t n_window, void* cuda_stream,
-                          int32_t* leaf_capacity_out, int32_t* knn_window_out);
+                          const int32_t* window_candidates, int32_t n_window, const int32_t* qpw_candidates,
+                          int32_t n_qpw, const int32_t* slot_candidates, int32_t n_slot, void* cuda_stream,
+                          sfc_batch_cloud* tuned_out);
 
 /* ---- batch plans: the batched pass recorded once as a CUDA graph and replayed --------- */
 

@@ -89,7 +89,8 @@ _SIGNATURES = {
                                      C.c_void_p]),
     "batch_free": (C.c_int, [C.c_void_p, C.c_void_p]),
     "batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_void_p, C.c_void_p, C.c_int32,
-                                 C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                 C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                 C.c_void_p]),
     "sfc_server_opts_default": (C.c_int, [C.c_void_p]),
     "server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -446,7 +447,8 @@ def search_stats():
 # ----------------------------------------------------------------------------- batched path
 class _BatchCloud(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("search", C.c_int32), ("kernel", C.c_int32), ("r", C.c_float),
-                ("k", C.c_int32), ("leaf_capacity", C.c_int32), ("knn_window", C.c_int32)]
+                ("k", C.c_int32), ("leaf_capacity", C.c_int32), ("knn_window", C.c_int32),
+                ("queries_per_warp", C.c_int32), ("record_slots", C.c_int32)]
 
 
 def _cloud_array(clouds: list):
@@ -455,7 +457,8 @@ def _cloud_array(clouds: list):
         radius = c.get("search", "radius") == "radius"
         arr[i] = _BatchCloud(int(c["n"]), 0 if radius else 1, _kern(c.get("kernel", "sphere")) if radius else 0,
                              float(c.get("r", 0.0)), int(c.get("k", 0)), int(c.get("leaf_capacity", 0)),
-                             int(c.get("knn_window", 0)))
+                             int(c.get("knn_window", 0)), int(c.get("queries_per_warp", 0)),
+                             int(c.get("record_slots", 0)))
     return arr
 
 
@@ -579,22 +582,29 @@ class BatchPlan(Batch):
 
 def batch_autotune(points: torch.Tensor, clouds: list, encoding="hilbert", leaf_capacity: int = 32,
                    prune: bool = True, leaf_candidates=(16, 32, 64, 128, 256), window_candidates=(8, 16, 32, 64),
-                   stream=None) -> list:
-    """``batch_autotune`` of the C ABI: the clouds with ``leaf_capacity`` and (kNN)
-    ``knn_window`` filled in from timing this batch on the device."""
+                   qpw_candidates=(16, 32), slot_candidates=(16, 32, 64), stream=None) -> list:
+    """``batch_autotune`` of the C ABI: the clouds with ``leaf_capacity``, (kNN)
+    ``knn_window``, ``queries_per_warp`` and (radius) ``record_slots`` filled in from timing
+    this batch on the device."""
     pts = _xyz(points, "points")
     if sum(int(c["n"]) for c in clouds) != pts.shape[0]:
         raise ValueError("the clouds' sizes must add up to the number of points")
     arr = _cloud_array(clouds)
     opts = _BuildOpts(int(leaf_capacity), 1 if prune else 0)
-    lc = (C.c_int32 * len(leaf_candidates))(*leaf_candidates)
-    wc = (C.c_int32 * len(window_candidates))(*window_candidates)
-    leaf_out = (C.c_int32 * len(clouds))()
-    win_out = (C.c_int32 * len(clouds))()
-    _check(lib().batch_autotune(_ptr(pts), C.byref(arr), len(clouds), _enc(encoding), C.byref(opts), lc,
-                                len(leaf_candidates), wc, len(window_candidates), C.c_void_p(_stream(stream)),
-                                leaf_out, win_out), "batch_autotune")
-    return [dict(c, leaf_capacity=int(leaf_out[i]), knn_window=int(win_out[i])) for i, c in enumerate(clouds)]
+
+    def ints(v):
+        return (C.c_int32 * max(len(v), 1))(*v), len(v)
+
+    lc, nl = ints(leaf_candidates)
+    wc, nw = ints(window_candidates)
+    qc, nq = ints(qpw_candidates)
+    sc, ns = ints(slot_candidates)
+    out = (_BatchCloud * len(clouds))()
+    _check(lib().batch_autotune(_ptr(pts), C.byref(arr), len(clouds), _enc(encoding), C.byref(opts), lc, nl, wc, nw,
+                                qc, nq, sc, ns, C.c_void_p(_stream(stream)), out), "batch_autotune")
+    return [dict(c, leaf_capacity=int(out[i].leaf_capacity), knn_window=int(out[i].knn_window),
+                 queries_per_warp=int(out[i].queries_per_warp), record_slots=int(out[i].record_slots))
+            for i, c in enumerate(clouds)]
 
 
 # ----------------------------------------------------------------------------- serving

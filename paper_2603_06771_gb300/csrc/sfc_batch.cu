@@ -466,6 +466,8 @@ struct BatchTables {
     std::vector<int64_t> out0;   // kNN clouds: first output entry
     int64_t knn_total = 0;
     int64_t rec_groups = 0;  // warp groups of the radius launches
+    int rec_cap[kLaunchSets] = {0, 0, 0, 0, 0, 0, 0, 0};  // record slots per group of each radius launch
+    int64_t rec_slots = 0;   // record slots of all radius launches
     int64_t int_bound = 0;   // internal nodes of all clouds at most
 };
 
@@ -495,11 +497,14 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
             q.r = c.r;
             q.r2 = c.r * c.r;
             q.window = c.knn_window > 0 ? c.knn_window : knn_default_window(c.k);
+            q.group_size = c.queries_per_warp > 0 ? c.queries_per_warp : 32;
             if (c.search == SFC_SEARCH_RADIUS) {
                 if (c.r > 0.f) {  // r <= 0: every row empty
                     q.row0 = p;
                     sets[c.kernel].push_back(q);
                     set_cloud[c.kernel].push_back(i);
+                    const int slots = c.record_slots > 0 ? c.record_slots : kRecordCap;
+                    if (slots > T.rec_cap[c.kernel]) T.rec_cap[c.kernel] = slots;
                 }
             } else {
                 q.row0 = T.knn_total;
@@ -519,12 +524,15 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
         int64_t g = 0;
         for (size_t j = 0; j < sets[t].size(); ++j) {
             sets[t][j].group0 = g;
-            g += (sets[t][j].nq + 31) / 32;
+            g += (sets[t][j].nq + sets[t][j].group_size - 1) / sets[t][j].group_size;
             T.table.push_back(sets[t][j]);
             T.table_cloud.push_back(set_cloud[t][j]);
         }
         T.groups[t] = g;
-        if (t < 4) T.rec_groups += g;
+        if (t < 4) {
+            T.rec_groups += g;
+            T.rec_slots += g * T.rec_cap[t];
+        }
     }
 }
 
@@ -589,7 +597,7 @@ static sfc_status alloc_trees(BatchBuffers& b, Scratch& m) {
 static void alloc_records(const BatchTables& T, BatchBuffers& b, Scratch& m) {
     b.rec = BatchRecords();
     if (T.rec_groups == 0) return;
-    const int64_t slots = T.rec_groups * kRecordCap;
+    const int64_t slots = T.rec_slots;
     BatchRecords r;
     if (m.try_alloc(&r.masks, 32 * slots) && m.try_alloc(&r.head, slots) && m.try_alloc(&r.count, T.rec_groups))
         b.rec = r;
@@ -661,11 +669,15 @@ static sfc_status enqueue_trees(const BatchTables& T, BatchBuffers& b, cudaStrea
 static BatchRecords records_of(const BatchTables& T, const BatchBuffers& b, int kern) {
     BatchRecords r;
     if (!b.rec.masks) return r;
-    int64_t g = 0;
-    for (int t = 0; t < kern; ++t) g += T.groups[t];
-    r.masks = b.rec.masks + g * kRecordCap * 32;
-    r.head = b.rec.head + g * kRecordCap;
+    int64_t g = 0, slot = 0;
+    for (int t = 0; t < kern; ++t) {
+        g += T.groups[t];
+        slot += T.groups[t] * T.rec_cap[t];
+    }
+    r.masks = b.rec.masks + slot * 32;
+    r.head = b.rec.head + slot;
     r.count = b.rec.count + g;
+    r.cap = T.rec_cap[kern];
     return r;
 }
 
@@ -717,6 +729,9 @@ static sfc_status check_batch_args(const sfc_batch_cloud* clouds, int32_t n_clou
     for (int i = 0; i < n_clouds; ++i) {
         const sfc_batch_cloud& c = clouds[i];
         if (c.n_points < 0 || c.leaf_capacity < 0 || c.knn_window < 0 || c.knn_window > 64) return SFC_ERR_INVALID;
+        if (c.queries_per_warp != 0 && c.queries_per_warp != 8 && c.queries_per_warp != 16 && c.queries_per_warp != 32)
+            return SFC_ERR_INVALID;
+        if (c.record_slots < 0 || c.record_slots > kRecordCapMax) return SFC_ERR_INVALID;
         if (c.search == SFC_SEARCH_RADIUS) {
             if (c.kernel < 0 || c.kernel > 3 || isnan(c.r)) return SFC_ERR_INVALID;
         } else if (c.search == SFC_SEARCH_KNN) {
@@ -1264,18 +1279,23 @@ sfc_status batch_plan_free(sfc_batch_plan p, void* cuda_stream) {
 
 sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds, int32_t n_clouds, sfc_encoding enc,
                           const sfc_build_opts* opts, const int32_t* leaf_candidates, int32_t n_leaf,
-                          const int32_t* window_candidates, int32_t n_window, void* cuda_stream,
-                          int32_t* leaf_capacity_out, int32_t* knn_window_out) {
+                          const int32_t* window_candidates, int32_t n_window, const int32_t* qpw_candidates,
+                          int32_t n_qpw, const int32_t* slot_candidates, int32_t n_slot, void* cuda_stream,
+                          sfc_batch_cloud* tuned_out) {
     sfc_build_opts o;
     int64_t total = 0;
     SFC_TRY(sfc::check_batch_args(clouds, n_clouds, enc, opts, &o, &total));
-    if (!leaf_capacity_out || !knn_window_out || n_leaf < 0 || n_window < 0 || (n_leaf > 0 && !leaf_candidates) ||
-        (n_window > 0 && !window_candidates))
+    if (!tuned_out || n_leaf < 0 || n_window < 0 || n_qpw < 0 || n_slot < 0 || (n_leaf > 0 && !leaf_candidates) ||
+        (n_window > 0 && !window_candidates) || (n_qpw > 0 && !qpw_candidates) || (n_slot > 0 && !slot_candidates))
         return SFC_ERR_INVALID;
     for (int i = 0; i < n_leaf; ++i)
         if (leaf_candidates[i] < 1) return SFC_ERR_INVALID;
     for (int i = 0; i < n_window; ++i)
         if (window_candidates[i] < 1 || window_candidates[i] > 64) return SFC_ERR_INVALID;
+    for (int i = 0; i < n_qpw; ++i)
+        if (qpw_candidates[i] != 8 && qpw_candidates[i] != 16 && qpw_candidates[i] != 32) return SFC_ERR_INVALID;
+    for (int i = 0; i < n_slot; ++i)
+        if (slot_candidates[i] < 1 || slot_candidates[i] > sfc::kRecordCapMax) return SFC_ERR_INVALID;
     if (total > 0 && (!points_xyz || !sfc::is_device_ptr(points_xyz))) return SFC_ERR_NOT_DEVICE_PTR;
     int dev = 0;
     SFC_CUDA(cudaGetDevice(&dev));
@@ -1288,56 +1308,66 @@ sfc_status batch_autotune(const float* points_xyz, const sfc_batch_cloud* clouds
         const int t = sfc::launch_set_of(c);
         if (t >= 0) set_points[t] += c.n_points;
     }
-    // leaf capacity per launch set: its searches plus its share of the build
-    int32_t best_leaf[kSets];
-    float best_cost[kSets];
-    for (int t = 0; t < kSets; ++t) {
-        best_leaf[t] = o.leaf_capacity;
-        best_cost[t] = INFINITY;
-    }
-    if (total > 0) {
-        for (int i = 0; i < n_leaf; ++i) {
-            for (auto& c : cl) {
-                c.leaf_capacity = leaf_candidates[i];
-                c.knn_window = 0;
-            }
+    // the current choice of every set; a knob whose candidate list is empty keeps the
+    // clouds' own values
+    int32_t leaf[kSets], window[kSets], qpw[kSets], slots[kSets];
+    for (int t = 0; t < kSets; ++t) leaf[t] = window[t] = qpw[t] = slots[t] = -1;
+    auto apply = [&]() {
+        for (int i = 0; i < n_clouds; ++i) {
+            const int t = sfc::launch_set_of(clouds[i]);
+            cl[i] = clouds[i];
+            if (t < 0) continue;
+            if (leaf[t] >= 0) cl[i].leaf_capacity = leaf[t];
+            if (window[t] >= 0 && t >= 4) cl[i].knn_window = window[t];
+            if (qpw[t] >= 0) cl[i].queries_per_warp = qpw[t];
+            if (slots[t] >= 0 && t < 4) cl[i].record_slots = slots[t];
+        }
+    };
+    // one timed pass per candidate of one knob (all sets at once): each set keeps the
+    // candidate with its least cost (its search time, plus its points' share of the build
+    // for the leaf capacity, which changes the build)
+    auto tune = [&](int32_t* knob, const int32_t* cand, int32_t n_cand, int t_lo, int t_hi, bool with_build,
+                    bool warm) -> sfc_status {
+        if (n_cand == 0 || total == 0) return SFC_OK;
+        float best[kSets];
+        int32_t pick[kSets];
+        for (int t = 0; t < kSets; ++t) {
+            best[t] = INFINITY;
+            pick[t] = knob[t];
+        }
+        for (int i = 0; i < n_cand; ++i) {
+            for (int t = t_lo; t < t_hi; ++t) knob[t] = cand[i];
+            apply();
             float build = 0.f, set_ms[kSets];
-            SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));  // warm
+            if (warm && i == 0) SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));
             SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));
-            for (int t = 0; t < kSets; ++t) {
+            for (int t = t_lo; t < t_hi; ++t) {
                 if (set_points[t] == 0) continue;
-                const float cost = set_ms[t] + build * static_cast<float>(set_points[t]) / static_cast<float>(total);
-                if (cost < best_cost[t]) {
-                    best_cost[t] = cost;
-                    best_leaf[t] = leaf_candidates[i];
+                const float cost = set_ms[t] + (with_build ? build * static_cast<float>(set_points[t]) /
+                                                                 static_cast<float>(total)
+                                                           : 0.f);
+                if (cost < best[t]) {
+                    best[t] = cost;
+                    pick[t] = cand[i];
                 }
             }
         }
-    }
-    // seeding window per kNN launch set, at the chosen leaf capacities
-    int32_t best_window[kSets] = {0, 0, 0, 0, 0, 0, 0, 0};
-    float best_knn[kSets];
-    for (int t = 0; t < kSets; ++t) best_knn[t] = INFINITY;
-    for (int i = 0; i < n_window && total > 0; ++i) {
-        for (auto& c : cl) {
-            const int t = sfc::launch_set_of(c);
-            c.leaf_capacity = t >= 0 ? best_leaf[t] : 0;
-            c.knn_window = window_candidates[i];
-        }
-        float build = 0.f, set_ms[kSets];
-        SFC_TRY(sfc::timed_pass(cl, points_xyz, enc, o, s, &build, set_ms));
-        for (int t = 4; t < kSets; ++t) {
-            if (set_points[t] == 0) continue;
-            if (set_ms[t] < best_knn[t]) {
-                best_knn[t] = set_ms[t];
-                best_window[t] = window_candidates[i];
-            }
-        }
-    }
+        for (int t = t_lo; t < t_hi; ++t) knob[t] = pick[t];
+        apply();
+        return SFC_OK;
+    };
+    SFC_TRY(tune(leaf, leaf_candidates, n_leaf, 0, kSets, true, true));
+    SFC_TRY(tune(window, window_candidates, n_window, 4, kSets, false, false));
+    SFC_TRY(tune(qpw, qpw_candidates, n_qpw, 0, kSets, false, false));
+    SFC_TRY(tune(slots, slot_candidates, n_slot, 0, 4, false, false));
+    apply();
     for (int i = 0; i < n_clouds; ++i) {
+        tuned_out[i] = cl[i];
+        if (tuned_out[i].leaf_capacity == 0) tuned_out[i].leaf_capacity = o.leaf_capacity;
         const int t = sfc::launch_set_of(clouds[i]);
-        leaf_capacity_out[i] = t >= 0 ? best_leaf[t] : o.leaf_capacity;
-        knn_window_out[i] = t >= 4 ? best_window[t] : 0;
+        if (t >= 0 && t < 4) tuned_out[i].knn_window = 0;
+        if (t < 0 || t >= 4) tuned_out[i].record_slots = 0;
+        if (t < 0) tuned_out[i].knn_window = 0;
     }
     return SFC_OK;
 }

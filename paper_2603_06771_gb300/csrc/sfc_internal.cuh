@@ -61,6 +61,7 @@ struct RadiusRecords {
 };
 constexpr uint32_t kRecordsOverflow = 0xffffffffu;
 constexpr int kRecordCap = 32;  // record slots per warp of 32 centres (more: the fill walks again)
+constexpr int kRecordCapMax = 128;  // the most record slots a batch cloud may ask for
 constexpr int kRecordCapSingle = 64;  // the same for the search of one cloud
 
 // The records of one batched radius launch: [groups][kRecordCap] slots (null: no records)
@@ -68,6 +69,7 @@ struct BatchRecords {
     uint32_t* masks = nullptr;
     uint2* head = nullptr;
     uint32_t* count = nullptr;
+    int cap = 0;  // slots per group
 };
 
 struct Octree {
@@ -104,7 +106,7 @@ struct SearchSeg {
     int32_t k;       // kNN: neighbours
     float r, r2;     // radius and fl(r * r)
     int32_t window;  // kNN: curve neighbours per side for the seeding window (0: none)
-    int32_t pad;
+    int32_t group_size;  // centres per warp group (8, 16 or 32; lanes beyond stay idle)
 };
 
 // Index of the cloud that owns warp group `group` (the last entry with group0 <= group).

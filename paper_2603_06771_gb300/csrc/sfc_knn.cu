@@ -306,11 +306,13 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
     int32_t root = 0;
     int k = a.k;
     int64_t window = a.window;
+    unsigned int gsize = 32;  // centres of this group (batched clouds may ask for fewer)
     if (a.segs) {
         if (group >= a.ngroups) return;
         if (a.skip && (*a.skip & a.skip_mask)) return;
         const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
-        first = sg.q0 + (group - sg.group0) * 32;
+        gsize = static_cast<unsigned int>(sg.group_size);
+        first = sg.q0 + (group - sg.group0) * gsize;
         q_lo = sg.q0;
         q_end = sg.q0 + sg.nq;
         out0 = sg.row0;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         return;
     }
     const int64_t qi = first + lane;
-    const bool active = qi < q_end;
+    const bool active = lane < gsize && qi < q_end;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     // first output entry of this lane's row
     const int64_t out_base = out0 + static_cast<int64_t>(__float_as_uint(c.w)) * k;

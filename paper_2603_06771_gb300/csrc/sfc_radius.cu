@@ -131,12 +131,14 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
     const int64_t group = static_cast<int64_t>(blockIdx.x) * kRadiusWarps + warp;
     int64_t first = group * 32, q_end = a.nq, row0 = 0;
     int32_t root = 0;
+    unsigned int gsize = 32;  // centres of this group (batched clouds may ask for fewer)
     float r = a.r, r2 = a.r2;
     if (a.segs) {
         if (group >= a.ngroups) return;  // whole warp
         if (a.skip && (*a.skip & a.skip_mask)) return;
         const SearchSeg sg = a.segs[find_search_seg(a.segs, a.nsegs, group)];
-        first = sg.q0 + (group - sg.group0) * 32;
+        gsize = static_cast<unsigned int>(sg.group_size);
+        first = sg.q0 + (group - sg.group0) * gsize;
         q_end = sg.q0 + sg.nq;
         row0 = sg.row0;
         root = sg.root;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(radius_warps<FILL>() * 32, FILL ? 18 : 32) k_r
         return;  // whole warp
     }
     const int64_t qi = first + lane;
-    const bool active = qi < q_end;
+    const bool active = lane < gsize && qi < q_end;
     const float4 c = active ? a.q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t row = row0 + __float_as_uint(c.w);
     if constexpr (!FILL) centre[warp][lane] = c;  // read by other lanes after the next __syncwarp
@@ -845,7 +847,7 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
     a.compact_factor = kCompactFactor;
     if (rec.masks) {  // the count pass records hit masks, the fill replays them
         a.rec_mode = fill ? 2 : 1;
-        a.rec_cap = kRecordCap;
+        a.rec_cap = rec.cap;
         a.rec_masks = rec.masks;
         a.rec_head = rec.head;
         a.rec_count = rec.count;

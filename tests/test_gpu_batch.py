@@ -301,10 +301,34 @@ def test_per_cloud_leaf_capacity_and_window_keep_results():
 def test_autotune_choices_are_valid_and_keep_results():
     xyz, specs = _random_batch(30, 23, 8000)
     pts = dev(np.concatenate(xyz))
-    tuned = sfc.batch_autotune(pts, specs, "hilbert", leaf_candidates=(16, 64), window_candidates=(16, 32))
+    tuned = sfc.batch_autotune(pts, specs, "hilbert", leaf_candidates=(16, 64), window_candidates=(16, 32),
+                               qpw_candidates=(8, 16, 32), slot_candidates=(4, 64))
     for sp, t in zip(specs, tuned):
+        searched = sp["n"] > 0 and (sp["search"] == "knn" or sp.get("r", 0) > 0)
         assert t["leaf_capacity"] in (16, 32, 64)  # 32: clouds without a search keep the default
         assert t["knn_window"] in ((16, 32) if sp["search"] == "knn" and sp["n"] > 0 else (0,))
+        assert t["queries_per_warp"] in ((8, 16, 32) if searched else (0,))
+        assert t["record_slots"] in ((4, 64) if searched and sp["search"] == "radius" else (0,))
     _same(sfc.batch_search(pts, tuned, "hilbert"), sfc.batch_search(pts, specs, "hilbert"), specs)
     with pytest.raises(sfc.SFCError):
         sfc.batch_autotune(pts, specs, "hilbert", window_candidates=(65,))
+    with pytest.raises(sfc.SFCError):
+        sfc.batch_autotune(pts, specs, "hilbert", qpw_candidates=(12,))
+    with pytest.raises(sfc.SFCError):
+        sfc.batch_autotune(pts, specs, "hilbert", slot_candidates=(0,))
+
+
+@pytest.mark.parametrize("qpw,slots", [(8, 1), (16, 3), (32, 128)])
+def test_queries_per_warp_and_record_slots_keep_results(qpw, slots):
+    """Every cloud walked by groups of 8, 16 or 32 centres, with 1 to 128 record slots per
+    group (1 slot: almost every group overflows and walks again in the fill), gives the
+    same bytes as the defaults."""
+    xyz, specs = _random_batch(20, 29, 6000)
+    pts = dev(np.concatenate(xyz))
+    knobbed = [dict(sp, queries_per_warp=qpw, record_slots=slots) for sp in specs]
+    _same(sfc.batch_search(pts, knobbed, "hilbert"), sfc.batch_search(pts, specs, "hilbert"), specs)
+    plan = sfc.BatchPlan(knobbed, "hilbert")
+    plan.points.copy_(pts)
+    plan.run()
+    _same(plan, sfc.batch_search(pts, specs, "hilbert"), specs)
+    plan.free()
