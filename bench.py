@@ -40,7 +40,7 @@ WORKLOAD = {
                    "10% buildings, 3 cm jitter)",
     "points": 10_000_000,
     "encoding": "hilbert",
-    "leaf_capacity": 64,
+    "leaf_capacity": 96,
     "radius": {"kernel": "sphere", "r": 2.0},
     "knn_k": 16,
 }
@@ -52,18 +52,18 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 203176960 + 1250478592, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
-    "radius_fill": {"bytes_per_launch": 3128745216 + 4302570240, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
-    "radius_count": {"bytes_per_launch": 322941696 + 921340672, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
+    "knn": {"bytes_per_launch": 190527744 + 1250124544, "sha256": "e96991fdc002bfffd6b90005f73ef7d0f71341d29171dd86a54c8ac966b49db0"},
+    "radius_fill": {"bytes_per_launch": 3165969152 + 4249615616, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "radius_count": {"bytes_per_launch": 309778944 + 912112128, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1553060916 / 62500, "sha256": "83a985fbbb312dab421dac79fca339c08cdbf7e44e398a86cc7b27bbce2b39af"},
-    "radius_count": {"warp_inst": 733115059 / 62500, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
-    "radius_fill": {"warp_inst": 627950257 / 62500, "sha256": "80180efbaa9098d384ca15daa67cddc747e0ba37cc844315d23bb2f91a9f7079"},
+    "knn": {"warp_inst": 1536210076 / 62500, "sha256": "e96991fdc002bfffd6b90005f73ef7d0f71341d29171dd86a54c8ac966b49db0"},
+    "radius_count": {"warp_inst": 714693086 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle

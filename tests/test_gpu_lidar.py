@@ -127,11 +127,11 @@ def test_knn_sampled_rows(tile, trees, enc, k):
 
 
 def test_every_row_sphere_r2_and_knn16_benchmark_config(tile):
-    """Every row of the benchmark's searches (Hilbert, leaf capacity 64): the oracle answers
+    """Every row of the benchmark's searches (Hilbert, leaf capacity 96): the oracle answers
     all 10M centres (its pointer octree, all host cores); neighbour sets are compared row by
     row after sorting each row by id on the device, kNN lists exactly."""
     xyz, p = tile["xyz"], tile["p"]
-    t = sfc.octree_build(tile["dev"], "hilbert", leaf_capacity=64)
+    t = sfc.octree_build(tile["dev"], "hilbert", leaf_capacity=96)
     rp, cols = sfc.radius_search(t, None, 2.0, "sphere")
     orp, ocols = p.tree.radius(xyz, 2.0, oracle.SPHERE)
     assert np.array_equal(rp.cpu().numpy(), orp)

@@ -23,7 +23,7 @@ def tile():
     xyz = synth.lidar_tile(N, synth.CONFIG_SEED[3])
     rows = np.sort(synth.Rng(3).integers(0, N_SAMPLE, N)).astype(np.int64)
     pts = torch.from_numpy(xyz).cuda()
-    tree = sfc.octree_build(pts, "hilbert", leaf_capacity=64)
+    tree = sfc.octree_build(pts, "hilbert", leaf_capacity=96)
     yield {"xyz": xyz, "rows": rows, "tree": tree}
     tree.free()
 
