@@ -111,6 +111,22 @@ def test_radius_all_points_uniform(kern, enc, prune):
     assert np.array_equal(cols, p.rows_by_rank(orp, ocol))
 
 
+@pytest.mark.parametrize("enc", ["morton", "hilbert"])
+@pytest.mark.parametrize("kern", KERNS)
+def test_radius_row_counts_more_radii(kern, enc):
+    """Row counts against the oracle at three more radii per kernel on the uniform cloud:
+    more pairs at the boundary of the binary32 test (a faster evaluation once decided one
+    pair of 30.6M differently at circle r = 0.024 and was dropped)."""
+    name, ncap = "uniform131k", 32
+    p = oracle_pipeline(name, enc, ncap)
+    t = sfc.octree_build(dev(p.xyz), enc, leaf_capacity=ncap)
+    for r in (0.017, 0.024, 0.031):
+        orp, _ = p.tree.radius(p.xyz, r, KERN[kern])  # not cached: only the row pointers are kept
+        rp, _ = sfc.radius_count(t, None, r, kern)
+        assert np.array_equal(rp.cpu().numpy(), orp), (kern, enc, r)
+    t.free()
+
+
 @pytest.mark.parametrize("enc", ENCS)
 @pytest.mark.parametrize("kern", KERNS)
 @pytest.mark.parametrize("r", [0.5, 2.0])
