@@ -271,15 +271,6 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
 template <int KMAX>
 __host__ __device__ constexpr int knn_warps() { return kKnnWarps; }
 
-__device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
-    NodeBox o;
-    o.lo = make_float4(__shfl_sync(0xffffffffu, b.lo.x, src), __shfl_sync(0xffffffffu, b.lo.y, src),
-                       __shfl_sync(0xffffffffu, b.lo.z, src), __shfl_sync(0xffffffffu, b.lo.w, src));
-    o.hi = make_float4(__shfl_sync(0xffffffffu, b.hi.x, src), __shfl_sync(0xffffffffu, b.hi.y, src),
-                       __shfl_sync(0xffffffffu, b.hi.z, src), __shfl_sync(0xffffffffu, b.hi.w, src));
-    return o;
-}
-
 // Group kNN walk.  Stack entries carry (first child, point range, lanes needing the node),
 // decided when the parent was expanded, so a pop reads shared memory only; an expansion
 // loads the eight children once (lanes 0-7).  Points (the seeding window, leaf chunks) are
@@ -288,15 +279,18 @@ __device__ __forceinline__ NodeBox shfl_node(const NodeBox& b, int src) {
 // and pass 2 lets each lane insert its marked points.
 // STATS: also accumulate the work counters of sfc_search_stats.
 template <int KMAX, bool STATS = false>
-// the minimum resident blocks match what shared memory allows for each list size (the
-// register budget never becomes the tighter limit)
-__global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX <= 16 ? 28 : (KMAX <= 32 ? 18 : 10)))
+// the minimum resident blocks match what shared memory allows for each list size: with
+// 8-byte stack entries 32 one-warp blocks fit for k <= 16 at 64 registers (k = 16 on the
+// 10M-point tile: 9.51 ms at 26 resident blocks, 9.10 ms at 32)
+__global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 16 ? 32 : (KMAX <= 32 ? 20 : 11))
     k_knn_group(KnnArgs a) {
     constexpr int kWarps = knn_warps<KMAX>();
     // staged points: the seeding window (32 + 2 window - 1 positions) or one leaf chunk
     constexpr int kBuf = KMAX <= 16 ? 64 : 32 + 2 * KMAX;
     static_assert(kBuf >= 64, "the walk keeps a chunk and the centres in the staging buffer");
-    __shared__ int4 stack_e[kWarps][kStackDepth];  // first child, start, end, lanes needing it
+    // x: an internal node's first child, or ~node for a leaf (its point range is read when it
+    // is popped); y: the lanes needing the node
+    __shared__ int2 stack_e[kWarps][kStackDepth];
     __shared__ uint64_t heaps[kWarps][KMAX][32];
     __shared__ float4 pbuf[kWarps][kBuf];
     const unsigned int lane = lane_id();
@@ -429,8 +423,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
         const unsigned int need = __ballot_sync(0xffffffffu, active && box_lower_bound(rb, c.x, c.y, c.z) <= best.kth_d2());
         if constexpr (STATS) st.v[kStBoxTests] += 1;
         if (need) {
-            if (lane == 0)
-                stack_e[warp][0] = make_int4(rc, __float_as_int(rb.lo.w), __float_as_int(rb.hi.w), static_cast<int>(need));
+            if (lane == 0) stack_e[warp][0] = make_int2(rc >= 0 ? rc : ~root, static_cast<int>(need));
             sp = 1;
         }
         __syncwarp();
@@ -441,11 +434,10 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
             break;
         }
         --sp;
-        const int4 e = stack_e[warp][sp];
+        const int2 e = stack_e[warp][sp];
         __syncwarp();
         const int32_t fc = e.x;
-        const uint32_t start = static_cast<uint32_t>(e.y), end = static_cast<uint32_t>(e.z);
-        const bool need = (static_cast<uint32_t>(e.w) >> lane) & 1u;
+        const bool need = (static_cast<uint32_t>(e.y) >> lane) & 1u;
         if (fc >= 0) {
             // the largest k-th distance of the group bounds what any lane still needs
             float mkd = active ? best.kth_d2() : -INFINITY;
@@ -460,6 +452,9 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
                 cc = a.child[fc + lane];
                 if (group_lower_bound(cb, glx, gly, glz, ghx, ghy, ghz) <= mkd)
                     key = child_order_key32(cb, gx, gy, gz, static_cast<int>(lane));
+                // the children's boxes for every lane, in the (idle) staging buffer
+                buf[2 * lane] = cb.lo;
+                buf[2 * lane + 1] = cb.hi;
             }
 #pragma unroll
             for (int size = 2; size <= 8; size <<= 1) {
@@ -477,18 +472,19 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
                 st.v[kStExpansions] += lane == 0;
                 st.v[kStBoxTests] += nvalid;
             }
+            __syncwarp();
             // push the farthest first so that the nearest is popped first
             for (int i = nvalid - 1; i >= 0; --i) {
                 const int ci = static_cast<int>(__shfl_sync(0xffffffffu, key, i) & 7u);
-                const NodeBox b = shfl_node(cb, ci);
+                NodeBox b;
+                b.lo = buf[2 * ci];
+                b.hi = buf[2 * ci + 1];
                 const int32_t bc = __shfl_sync(0xffffffffu, cc, ci);
                 const unsigned int cneed =
                     __ballot_sync(0xffffffffu, active && box_lower_bound(b, c.x, c.y, c.z) <= best.kth_d2());
                 if (cneed) {
                     if (sp < kStackDepth) {
-                        if (lane == 0)
-                            stack_e[warp][sp] = make_int4(bc, __float_as_int(b.lo.w), __float_as_int(b.hi.w),
-                                                          static_cast<int>(cneed));
+                        if (lane == 0) stack_e[warp][sp] = make_int2(bc >= 0 ? bc : ~(fc + ci), static_cast<int>(cneed));
                         ++sp;
                     } else {
                         guard_ok = false;
@@ -497,6 +493,9 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 8 ? 32 : (KMAX
             }
             __syncwarp();
         } else {
+            // a leaf: its point range from the node table
+            const NodeBox* const lb = a.nodes + ~fc;
+            const uint32_t start = __float_as_uint(__ldg(&lb->lo.w)), end = __float_as_uint(__ldg(&lb->hi.w));
             const unsigned int needing = __ballot_sync(0xffffffffu, need);
             const uint32_t n_need = static_cast<uint32_t>(__popc(needing));
             if constexpr (STATS) st.v[kStLeaves] += lane == 0;
