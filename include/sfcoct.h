@@ -244,8 +244,9 @@ sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, 
                         const sfc_build_opts* opts, void* cuda_stream, sfc_batch* out);
 
 /* Device views of one cloud's results (no copy, valid until batch_free):
- *   radius cloud: row_ptr has n_points + 1 entries whose values index *cols from its start,
- *                 *nnz = row_ptr[n_points] - row_ptr[0]; knn pointers are NULL.
+ *   radius cloud: the cloud's own CSR: row_ptr has n_points + 1 entries, row_ptr[0] == 0,
+ *                 and row i is cols[row_ptr[i] .. row_ptr[i + 1]); *nnz = row_ptr[n_points];
+ *                 knn pointers are NULL.
  *   kNN cloud:    knn_idx / knn_d2 hold n_points x k entries (layout of knn()); the CSR
  *                 pointers are NULL and *nnz = 0. */
 sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_ptr, const int32_t** cols,

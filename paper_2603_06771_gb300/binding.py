@@ -480,17 +480,16 @@ class Batch:
         return rp.value, cols.value, int(nnz.value), knn_i.value, knn_d.value
 
     def radius(self, i: int):
-        """(row_ptr, cols) of radius cloud i, row_ptr rebased to start at 0 (torch tensors)."""
+        """(row_ptr, cols) of radius cloud i as the library hands them out: row_ptr starts at
+        0 and cols at the cloud's first neighbour (torch views of library memory)."""
         if self._h is None:
             raise RuntimeError("batch already freed")
         rp, cols, nnz, _, _ = self._views(i)
         n = self.clouds[i]["n"]
         row_ptr = torch.as_tensor(_DeviceArray(self, rp, n + 1, "<i8"), device="cuda")
-        first = int(row_ptr[0].item())
         if nnz == 0:  # (the address may lie just past the output array)
-            return row_ptr - first, torch.empty(0, dtype=torch.int32, device="cuda")
-        col = torch.as_tensor(_DeviceArray(self, cols + 4 * first, nnz, "<i4"), device="cuda")
-        return row_ptr - first, col
+            return row_ptr, torch.empty(0, dtype=torch.int32, device="cuda")
+        return row_ptr, torch.as_tensor(_DeviceArray(self, cols, nnz, "<i4"), device="cuda")
 
     def knn(self, i: int):
         """(idx [n, k], d2 [n, k]) of kNN cloud i (torch tensors)."""

@@ -421,6 +421,24 @@ __global__ void k_batch_row_bounds(const int64_t* __restrict__ row_ptr, const in
     if (i < n) out[i] = row_ptr[where[i]];
 }
 
+// Every cloud's own row pointers, starting at 0: cloud c's n_c + 1 entries sit at
+// [p0_c + c, p0_c + c + n_c] of rel (the batch's row pointers minus the cloud's first).
+__global__ void k_batch_rel_rows(const int64_t* __restrict__ row_ptr, const BatchSeg* __restrict__ segs, int nsegs,
+                                 int64_t total, int64_t* __restrict__ rel) {
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = nsegs - 1;  // the last cloud c with p0_c + c <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].p0 + mid <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t p0 = segs[lo].p0;
+        const int64_t i = g - lo - p0;  // 0 .. n_c
+        rel[g] = row_ptr[p0 + i] - row_ptr[p0];
+    }
+}
+
 }  // namespace sfc
 
 // ---------------------------------------------------------------------------------
@@ -705,7 +723,7 @@ static sfc_status enqueue_radius_count(const BatchTables& T, BatchBuffers& b, in
 
 // The fill pass into cols (capacity cols_cap), then every cloud's row bounds.
 static sfc_status enqueue_radius_fill(const BatchTables& T, BatchBuffers& b, int prune, const int64_t* row_ptr,
-                                      int32_t* cols, int64_t cols_cap, cudaStream_t s) {
+                                      int32_t* cols, int64_t cols_cap, int64_t* rel_rows, cudaStream_t s) {
     SFC_LAUNCH("batch_check_cols", s, k_batch_check_cols, 1, 1, 0, row_ptr + T.n_total, cols_cap, b.tot);
     for (int kern = 0; kern < 4; ++kern)
         SFC_TRY(batch_radius_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[kern],
@@ -714,6 +732,9 @@ static sfc_status enqueue_radius_fill(const BatchTables& T, BatchBuffers& b, int
                                     kOverNodes | kOverCols | kNonFinite, s));
     SFC_LAUNCH("batch_row_bounds", s, k_batch_row_bounds, grid_for(static_cast<int64_t>(T.where.size()), 128), 128, 0,
                row_ptr, b.where, static_cast<int>(T.where.size()), b.bounds);
+    const int64_t rel_total = T.n_total + T.n_clouds;
+    SFC_LAUNCH("batch_rel_rows", s, k_batch_rel_rows, grid_for(rel_total, 256, 152 * 8), 256, 0, row_ptr, b.segs,
+               T.n_clouds, rel_total, rel_rows);
     return SFC_OK;
 }
 
@@ -757,6 +778,7 @@ struct sfc_batch_s {
     std::vector<int64_t> row_lo, row_hi;  // radius clouds: row_ptr[p0], row_ptr[p0 + n]
     int64_t nnz = 0;
     int64_t* row_ptr = nullptr;
+    int64_t* rel_rows = nullptr;  // every cloud's row pointers, starting at 0 (see k_batch_rel_rows)
     int32_t* cols = nullptr;
     int32_t* knn_idx = nullptr;
     float* knn_d2 = nullptr;
@@ -824,7 +846,8 @@ static sfc_status run_batch(sfc_batch_s* B, const float* xyz, int enc, const sfc
     SFC_CUDA(cudaMemcpyAsync(&B->nnz, B->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
     SFC_TRY(dev_alloc(&B->cols, B->nnz, s));
-    SFC_TRY(enqueue_radius_fill(T, b, o.prune, B->row_ptr, B->cols, B->nnz, s));
+    SFC_TRY(dev_alloc(&B->rel_rows, n + T.n_clouds, s));
+    SFC_TRY(enqueue_radius_fill(T, b, o.prune, B->row_ptr, B->cols, B->nnz, B->rel_rows, s));
     std::vector<int64_t> bounds(T.where.size());
     unsigned int herr = 0;
     SFC_CUDA(cudaMemcpyAsync(bounds.data(), b.bounds, sizeof(int64_t) * bounds.size(), cudaMemcpyDeviceToHost, s));
@@ -840,6 +863,8 @@ static sfc_status run_batch(sfc_batch_s* B, const float* xyz, int enc, const sfc
 
 static void free_batch(sfc_batch_s* B, cudaStream_t s) {
     dev_free(B->row_ptr, s);
+    dev_free(B->rel_rows, s);
+    B->rel_rows = nullptr;
     dev_free(B->cols, s);
     dev_free(B->knn_idx, s);
     dev_free(B->knn_d2, s);
@@ -850,13 +875,13 @@ static void free_batch(sfc_batch_s* B, cudaStream_t s) {
 }
 
 // views of one cloud's results (shared by batches and plans)
-static sfc_status cloud_views(const BatchTables& T, int32_t cloud, const int64_t* row_ptr, const int32_t* cols,
+static sfc_status cloud_views(const BatchTables& T, int32_t cloud, const int64_t* rel_rows, const int32_t* cols,
                               const int32_t* knn_idx, const float* knn_d2, const std::vector<int64_t>& row_lo,
                               const std::vector<int64_t>& row_hi, const int64_t** rp, const int32_t** cl,
                               int64_t* nnz, const int32_t** ki, const float** kd, const sfc_batch_cloud& c) {
     const bool radius = c.search == SFC_SEARCH_RADIUS;
-    if (rp) *rp = radius ? row_ptr + T.seg[cloud].p0 : nullptr;
-    if (cl) *cl = radius ? cols : nullptr;
+    if (rp) *rp = radius ? rel_rows + T.seg[cloud].p0 + cloud : nullptr;
+    if (cl) *cl = radius ? cols + row_lo[cloud] : nullptr;
     if (nnz) *nnz = radius ? row_hi[cloud] - row_lo[cloud] : 0;
     if (ki) *ki = radius ? nullptr : knn_idx + T.out0[cloud];
     if (kd) *kd = radius ? nullptr : knn_d2 + T.out0[cloud];
@@ -993,6 +1018,7 @@ struct sfc_batch_plan_s {
     sfc::BatchBuffers b;
     float* xyz = nullptr;
     int64_t* row_ptr = nullptr;
+    int64_t* rel_rows = nullptr;  // every cloud's row pointers, starting at 0
     int32_t* cols = nullptr;
     int64_t cols_cap = 0;
     int32_t* knn_idx = nullptr;
@@ -1037,7 +1063,8 @@ static sfc_status capture_plan(sfc_batch_plan_s* P) {
         if (st == SFC_OK && (st = P->side.fork(s)) == SFC_OK) forked = true;  // kNN beside the radius launches
         if (st == SFC_OK) st = enqueue_knn(P->T, b, P->knn_idx, P->knn_d2, P->side.s2);
         if (st == SFC_OK) st = enqueue_radius_count(P->T, b, P->o.prune, P->row_ptr, s, tmp);
-        if (st == SFC_OK) st = enqueue_radius_fill(P->T, b, P->o.prune, P->row_ptr, P->cols, P->cols_cap, s);
+        if (st == SFC_OK)
+            st = enqueue_radius_fill(P->T, b, P->o.prune, P->row_ptr, P->cols, P->cols_cap, P->rel_rows, s);
         if (forked) {  // the capture must end on one stream
             const sfc_status js = P->side.join(s);
             if (st == SFC_OK) st = js;
@@ -1120,6 +1147,9 @@ sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, 
     if (st == SFC_OK && total == 0) {
         st = sfc::dev_alloc(&B->row_ptr, 1, s);
         if (st == SFC_OK && cudaMemsetAsync(B->row_ptr, 0, sizeof(int64_t), s) != cudaSuccess) st = SFC_ERR_CUDA;
+        if (st == SFC_OK) st = sfc::dev_alloc(&B->rel_rows, n_clouds, s);
+        if (st == SFC_OK && cudaMemsetAsync(B->rel_rows, 0, sizeof(int64_t) * n_clouds, s) != cudaSuccess)
+            st = SFC_ERR_CUDA;
     }
     if (st != SFC_OK) {
         sfc::free_batch(B, s);
@@ -1133,7 +1163,7 @@ sfc_status batch_search(const float* points_xyz, const sfc_batch_cloud* clouds, 
 sfc_status batch_cloud_result(sfc_batch b, int32_t cloud, const int64_t** row_ptr, const int32_t** cols, int64_t* nnz,
                               const int32_t** knn_idx, const float** knn_d2) {
     if (!b || cloud < 0 || cloud >= b->T.n_clouds) return SFC_ERR_INVALID;
-    return sfc::cloud_views(b->T, cloud, b->row_ptr, b->cols, b->knn_idx, b->knn_d2, b->row_lo, b->row_hi, row_ptr,
+    return sfc::cloud_views(b->T, cloud, b->rel_rows, b->cols, b->knn_idx, b->knn_d2, b->row_lo, b->row_hi, row_ptr,
                             cols, nnz, knn_idx, knn_d2, b->clouds_[cloud]);
 }
 
@@ -1188,7 +1218,8 @@ sfc_status batch_plan_create(const sfc_batch_cloud* clouds, int32_t n_clouds, sf
         for (int64_t j = 0; j < P->T.count[t]; ++j) radius_points += P->T.table[P->T.off[t] + j].nq;
     P->cols_cap = nnz_capacity > 0 ? nnz_capacity : 64 * radius_points;
     if ((st = m.alloc(&P->xyz, 3 * n)) != SFC_OK || (st = sfc::alloc_base(P->T, P->b, m)) != SFC_OK ||
-        (st = m.alloc(&P->row_ptr, n + 1)) != SFC_OK || (st = m.alloc(&P->knn_idx, P->T.knn_total)) != SFC_OK ||
+        (st = m.alloc(&P->row_ptr, n + 1)) != SFC_OK || (st = m.alloc(&P->rel_rows, n + n_clouds)) != SFC_OK ||
+        (st = m.alloc(&P->knn_idx, P->T.knn_total)) != SFC_OK ||
         (st = m.alloc(&P->knn_d2, P->T.knn_total)) != SFC_OK ||
         (st = sfc::dev_alloc(&P->cols, P->cols_cap, P->cs)) != SFC_OK ||
         (st = sfc::plan_alloc_trees(P, P->T.int_bound)) != SFC_OK)
@@ -1247,7 +1278,7 @@ sfc_status batch_plan_finish(sfc_batch_plan p, void* cuda_stream) {
         SFC_CUDA(cudaStreamSynchronize(p->cs));
         const unsigned int keep = tot.flags & ~sfc::kOverCols;
         SFC_CUDA(cudaMemcpyAsync(&p->b.tot->flags, &keep, sizeof keep, cudaMemcpyHostToDevice, s));
-        SFC_TRY(sfc::enqueue_radius_fill(p->T, p->b, p->o.prune, p->row_ptr, p->cols, p->cols_cap, s));
+        SFC_TRY(sfc::enqueue_radius_fill(p->T, p->b, p->o.prune, p->row_ptr, p->cols, p->cols_cap, p->rel_rows, s));
         SFC_CUDA(cudaMemcpyAsync(p->host_bounds, p->b.bounds, sizeof(int64_t) * p->T.where.size(),
                                  cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaMemcpyAsync(&p->host->err, p->b.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -1265,7 +1296,7 @@ sfc_status batch_plan_finish(sfc_batch_plan p, void* cuda_stream) {
 sfc_status batch_plan_result(sfc_batch_plan p, int32_t cloud, const int64_t** row_ptr, const int32_t** cols,
                              int64_t* nnz, const int32_t** knn_idx, const float** knn_d2) {
     if (!p || !p->ready || cloud < 0 || cloud >= p->T.n_clouds) return SFC_ERR_INVALID;
-    return sfc::cloud_views(p->T, cloud, p->row_ptr, p->cols, p->knn_idx, p->knn_d2, p->row_lo, p->row_hi, row_ptr,
+    return sfc::cloud_views(p->T, cloud, p->rel_rows, p->cols, p->knn_idx, p->knn_d2, p->row_lo, p->row_hi, row_ptr,
                             cols, nnz, knn_idx, knn_d2, p->clouds[cloud]);
 }
 

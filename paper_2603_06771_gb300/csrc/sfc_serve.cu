@@ -65,18 +65,8 @@ struct Request {
     int32_t* knn_idx = nullptr;
     float* knn_d2 = nullptr;
     int64_t rows = 0;
-    int64_t* own_row_ptr = nullptr;  // a merged radius request's row pointers, starting at 0
-    int64_t row_base = 0;            // ... and where its rows start in the batch's neighbour array
-    cudaStream_t stream = nullptr;   // where its results were made (frees go there)
+    cudaStream_t stream = nullptr;  // where its results were made (frees go there)
 };
-
-// A merged request's rows inside the batch's CSR start at rp[0]; its own copy starts at 0.
-__global__ void k_rebase_rows(const int64_t* __restrict__ rp, int64_t n, int64_t* __restrict__ out) {
-    const int64_t base = rp[0];
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i <= n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        out[i] = rp[i] - base;
-}
 
 int64_t estimate(const sfc_request& r) {
     const int64_t rows = r.queries_xyz ? r.n_queries : r.n_points;
@@ -185,10 +175,6 @@ sfc_status run_merged(sfc_server_s* S, std::vector<Request*>& group, cudaStream_
             const int64_t* rp = nullptr;
             const int32_t* cols = nullptr;
             SFC_TRY(batch_cloud_result(pass->batch, q.cloud, &rp, &cols, &q.csr.nnz, nullptr, nullptr));
-            SFC_CUDA(cudaMemcpyAsync(&q.row_base, rp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            SFC_TRY(sfc::dev_alloc(&q.own_row_ptr, q.rows + 1, s));
-            SFC_LAUNCH("serve_rebase_rows", s, k_rebase_rows, sfc::grid_for(q.rows + 1, 256, 152 * 8), 256, 0, rp,
-                       q.rows, q.own_row_ptr);
         }
     }
     SFC_CUDA(cudaStreamSynchronize(s));
@@ -197,8 +183,6 @@ sfc_status run_merged(sfc_server_s* S, std::vector<Request*>& group, cudaStream_
 
 void release_single(Request& q) {
     if (q.csr.row_ptr || q.csr.cols) sfc_csr_free(&q.csr, q.stream);
-    sfc::dev_free(q.own_row_ptr, q.stream);
-    q.own_row_ptr = nullptr;
     sfc::dev_free(q.knn_idx, q.stream);
     sfc::dev_free(q.knn_d2, q.stream);
     if (q.tree) octree_free(q.tree, q.stream);
@@ -265,8 +249,6 @@ void worker(sfc_server_s* S, int slot) {
                 q->cloud = -1;
                 q->batched_with = 1;
                 q->csr = sfc_csr{};
-                sfc::dev_free(q->own_row_ptr, s);
-                q->own_row_ptr = nullptr;
             }
             pass.reset();
             for (size_t i = 0; i < group.size(); ++i) {
@@ -414,8 +396,8 @@ sfc_status server_result(sfc_server S, int64_t id, sfc_request_result* out) {
         const float* kd = nullptr;
         int64_t nnz = 0;
         SFC_TRY(batch_cloud_result(q.pass->batch, q.cloud, &rp, &cols, &nnz, &ki, &kd));
-        out->row_ptr = q.own_row_ptr;  // rebased on the device when the pass finished
-        out->cols = cols ? cols + q.row_base : nullptr;
+        out->row_ptr = rp;  // the batch hands out every cloud's rows starting at 0
+        out->cols = cols;
         out->nnz = nnz;
         out->knn_idx = ki;
         out->knn_d2 = kd;
