@@ -52,16 +52,16 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 190527744 + 1250124544, "sha256": "e96991fdc002bfffd6b90005f73ef7d0f71341d29171dd86a54c8ac966b49db0"},
-    "radius_fill": {"bytes_per_launch": 3165969152 + 4249615616, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
-    "radius_count": {"bytes_per_launch": 309778944 + 912112128, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "knn": {"bytes_per_launch": 190629888 + 1250618112, "sha256": "11d93c968d4290235f3fdf1c27cd76d5ebec6a03eeefa61045a25c295ced3138"},
+    "radius_fill": {"bytes_per_launch": 3166897408 + 4249998848, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "radius_count": {"bytes_per_launch": 310978560 + 912199680, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1536210076 / 62500, "sha256": "e96991fdc002bfffd6b90005f73ef7d0f71341d29171dd86a54c8ac966b49db0"},
+    "knn": {"warp_inst": 1551432897 / 62500, "sha256": "11d93c968d4290235f3fdf1c27cd76d5ebec6a03eeefa61045a25c295ced3138"},
     "radius_count": {"warp_inst": 714693086 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
     "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
 }
