@@ -60,11 +60,12 @@ struct RadiusRecords {
     bool valid = false;
 };
 constexpr uint32_t kRecordsOverflow = 0xffffffffu;
-constexpr int kRecordCap = 32;  // record slots per warp of 32 centres (more: the fill walks again)
-constexpr int kRecordCapMax = 128;  // the most record slots a batch cloud may ask for
-constexpr int kRecordCapSingle = 64;  // the same for the search of one cloud
+constexpr int kRecordCap = 32;        // record slots per warp group of a batch cloud by default
+                                      // (a group with more leaf chunks walks again in the fill)
+constexpr int kRecordCapMax = 128;    // the most record slots a batch cloud may ask for
+constexpr int kRecordCapSingle = 64;  // record slots per warp group of a single-cloud search
 
-// The records of one batched radius launch: [groups][kRecordCap] slots (null: no records)
+// The records of one batched radius launch: [groups][cap] slots (null: no records)
 struct BatchRecords {
     uint32_t* masks = nullptr;
     uint2* head = nullptr;

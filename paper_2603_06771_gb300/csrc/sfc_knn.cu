@@ -266,14 +266,14 @@ __device__ __forceinline__ float group_lower_bound(const NodeBox& b, float glx, 
                    fmaxf(fmaxf(__fsub_rn(b.lo.z, ghz), __fsub_rn(glz, b.hi.z)), 0.0f));
 }
 
-// resident blocks per SM the register budget is sized for (4 warps each)
 // warps per block of the group kernel
 template <int KMAX>
 __host__ __device__ constexpr int knn_warps() { return kKnnWarps; }
 
-// Group kNN walk.  Stack entries carry (first child, point range, lanes needing the node),
-// decided when the parent was expanded, so a pop reads shared memory only; an expansion
-// loads the eight children once (lanes 0-7).  Points (the seeding window, leaf chunks) are
+// Group kNN walk.  Stack entries carry (an internal node's first child or a leaf's node
+// index, lanes needing the node), decided when the parent was expanded; a popped leaf reads
+// its point range from the node table; an expansion loads the eight children once (lanes
+// 0-7) and stages their boxes in shared memory for every lane.  Points (the seeding window, leaf chunks) are
 // staged in shared memory with coalesced loads, and both the tests and the insertions read
 // them there.  Per chunk, pass 1 marks the points that beat each lane's current k-th pair
 // and pass 2 lets each lane insert its marked points.

@@ -5,7 +5,8 @@
 // Work layout.  For a cloud ordered along the curve, a warp takes 32 consecutive
 // centres in curve order (they are close in space) and walks the octree once for all of
 // them: one lane per centre, the node stack shared in shared memory, a node entered when
-// any lane's kernel may reach its box.  Leaf points are read with warp-uniform loads and
+// any lane's kernel may reach its box (for a compact group of centres: when the group's box
+// may, the lanes deciding at the leaves).  Leaf points are read with warp-uniform loads and
 // tested by every lane against its own centre; hits become a 32-bit mask per lane, and
 // the warp writes each lane's hits as one contiguous run of its output row.  For the
 // unordered cloud (SFC_ENC_NONE) the 32 centres of a warp are scattered, so each lane
