@@ -216,7 +216,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, k: int) -> float | None:
         "radius_count": 12 * n + 4 * n,                  # points, counts
         "knn": 16 * n + 8 * n * k,                       # points + ids, k (id, d2) pairs per centre
         "radix_scatter": 24 * n,                         # read + write (code, index)
-        "radix_histogram": 8 * n,
+        "radix_count": 8 * n,                            # one read of the codes for every pass
         "encode": 12 * n + 12 * n,
         "gather_points": 16 * n + 16 * n,
         "bbox": 12 * n,

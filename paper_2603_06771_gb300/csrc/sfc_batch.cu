@@ -647,12 +647,12 @@ static sfc_status enqueue_order(const BatchTables& T, BatchBuffers& b, const flo
     SFC_LAUNCH("batch_bbox_finish", s, k_batch_bbox_finish, sgrid, 128, 0, b.segs, nsegs);
     SFC_TRY(batch_encode(xyz, n, enc, b.segs, nsegs, b.codes, b.v0, s));
     SFC_CUDA(cudaMemcpyAsync(b.k0, b.codes, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
-    SFC_TRY(radix_sort_pairs(b.k0, b.v0, b.k1, b.v1, n, s, tmp));
+    SFC_TRY(radix_sort_pairs(b.k0, b.v0, b.k1, b.v1, n, s, tmp, b.err));
     if (nsegs > 1) {  // stable pass on the cloud number: order (cloud, code)
         SFC_LAUNCH("batch_cloud_keys", s, k_batch_cloud_keys, grid, 256, 0, b.v0, n, b.segs, nsegs, b.k0);
         int bits = 0;
         while ((1 << bits) < nsegs) ++bits;
-        SFC_TRY(radix_sort_pairs_bits(b.k0, b.v0, b.k1, b.v1, n, 0, bits, s, tmp));
+        SFC_TRY(radix_sort_pairs_bits(b.k0, b.v0, b.k1, b.v1, n, 0, bits, s, tmp, b.err));
     }
     // k1 receives the sorted codes
     SFC_LAUNCH("batch_gather", s, k_batch_gather, grid, 256, 0, xyz, n, b.codes, b.v0, b.segs, nsegs, b.k1, b.pts,
@@ -857,7 +857,7 @@ static sfc_status run_batch(sfc_batch_s* B, const float* xyz, int enc, const sfc
         B->row_lo[i] = bounds[2 * i];
         B->row_hi[i] = bounds[2 * i + 1];
     }
-    if (herr & kGuardTripped) return SFC_ERR_INTERNAL;
+    SFC_TRY(guard_status(herr));
     return SFC_OK;
 }
 
@@ -986,7 +986,7 @@ static sfc_status timed_pass(const std::vector<sfc_batch_cloud>& clouds, const f
     unsigned int herr = 0;
     SFC_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof herr, cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
-    if (herr & kGuardTripped) return SFC_ERR_INTERNAL;
+    SFC_TRY(guard_status(herr));
     *build_ms = ev.ms(e0, ea) + ev.ms(e1, e2);  // the host wait between the two is not build time
     for (int kern = 0; kern < 4; ++kern) set_ms[kern] = ev.ms(mc[kern][0], mc[kern][1]) + ev.ms(mf[kern][0], mf[kern][1]);
     for (int t = 4; t < kLaunchSets; ++t) set_ms[t] = ev.ms(mk[t][0], mk[t][1]);
@@ -1284,7 +1284,7 @@ sfc_status batch_plan_finish(sfc_batch_plan p, void* cuda_stream) {
         SFC_CUDA(cudaMemcpyAsync(&p->host->err, p->b.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaStreamSynchronize(s));
     }
-    if (p->host->err & sfc::kGuardTripped) return SFC_ERR_INTERNAL;
+    SFC_TRY(sfc::guard_status(p->host->err));
     for (int i = 0; i < p->T.n_clouds; ++i) {
         p->row_lo[i] = p->host_bounds[2 * i];
         p->row_hi[i] = p->host_bounds[2 * i + 1];

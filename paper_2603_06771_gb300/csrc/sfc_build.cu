@@ -408,7 +408,7 @@ sfc_status prepare_queries(const Octree* h, const float* queries, int64_t nq, cu
         SFC_LAUNCH("query_codes", s, k_query_codes<SFC_ENC_HILBERT>, grid, 256, 0, queries, nq, h->scal, k0, v0, bad);
     else
         SFC_LAUNCH("query_codes", s, k_query_codes<SFC_ENC_MORTON>, grid, 256, 0, queries, nq, h->scal, k0, v0, bad);
-    SFC_TRY(radix_sort_pairs(k0, v0, k1, v1, nq, s, scratch));
+    SFC_TRY(radix_sort_pairs(k0, v0, k1, v1, nq, s, scratch, &h->scal->bad));
     SFC_LAUNCH("gather_queries", s, k_gather_queries, grid, 256, 0, queries, nq, v0, out);
     return SFC_OK;
 }
@@ -451,7 +451,7 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
         else
             SFC_LAUNCH("encode", s, k_encode<SFC_ENC_MORTON>, grid, 256, 0, xyz, n, t->scal, t->keys, t->perm);
         // section 4: ascending codes, ties in input order
-        SFC_TRY(radix_sort_pairs(t->keys, t->perm, keys_alt, perm_alt, n, s, scratch));
+        SFC_TRY(radix_sort_pairs(t->keys, t->perm, keys_alt, perm_alt, n, s, scratch, &t->scal->bad));
         if (t->enc == SFC_ENC_NONE)
             SFC_LAUNCH("pack_points", s, k_pack_points, grid, 256, 0, xyz, n, t->pts, (unsigned int*)nullptr);
         else
@@ -467,6 +467,7 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
         SFC_CUDA(cudaMemcpyAsync(&n_int, first + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaMemcpyAsync(&hs, t->scal, sizeof(BuildScalars), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaStreamSynchronize(s));
+        if (hs.bad & kWaitTimedOut) return SFC_ERR_TIMEOUT;
         if (hs.bad) return SFC_ERR_NOT_FINITE;
         for (int a = 0; a < 3; ++a) t->lo[a] = hs.lo[a];
         t->scale = hs.scale;

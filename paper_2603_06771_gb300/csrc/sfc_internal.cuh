@@ -29,6 +29,7 @@ constexpr uint32_t kCellMax = (1u << kLevels) - 1;
 constexpr int kMaxK = 64;                          // largest k of the kNN kernels
 constexpr int kStackDepth = 160;                   // >= 7 * 21 + 8 pending nodes of a depth-first walk
 constexpr unsigned int kGuardTripped = 4u;          // BuildScalars::bad bit set by a failed guard
+constexpr unsigned int kWaitTimedOut = 8u;          // the same word: a bounded device-side wait gave up
 
 struct __align__(16) NodeBox {
     float4 lo;  // w: start (uint32 bits)
@@ -210,10 +211,12 @@ sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n,
 sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_t s, uint32_t* counts,
                                  int64_t* tile_sums, int64_t* row_ptr, int64_t* nnz);
 
-// Stable LSD radix sort of (key, value) pairs by the low 63 bits of key; the result ends
-// in keys / vals, keys_alt / vals_alt are work buffers of the same size.
+// Stable LSD radix sort of (key, value) pairs by the 64 bits of key; the result ends in
+// keys / vals, keys_alt / vals_alt are work buffers of the same size.  n < 2^32.  fault
+// (device, may be null) gets kWaitTimedOut if a tile's bounded wait for the counts of
+// the tiles before it gave up (the order is then wrong); the sort never synchronises.
 sfc_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                            cudaStream_t s, Scratch& scratch);
+                            cudaStream_t s, Scratch& scratch, unsigned int* fault);
 
 // Centres of a search in processing order: float4 (x, y, z, output row bits).  For
 // queries == NULL the tree points themselves; otherwise caller centres, sorted by their
@@ -243,6 +246,13 @@ sfc_status prepare_queries(const Octree* h, const float* queries, int64_t nq, cu
         kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__); \
         SFC_TRY(::sfc::launch_end(name, stream));                  \
     } while (0)
+
+// The status of the guard bits of a BuildScalars::bad (or batch error) word read back.
+inline sfc_status guard_status(unsigned int bad) {
+    if (bad & kGuardTripped) return SFC_ERR_INTERNAL;
+    if (bad & kWaitTimedOut) return SFC_ERR_TIMEOUT;
+    return SFC_OK;
+}
 
 inline unsigned int grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {
     int64_t g = (n + threads - 1) / threads;
@@ -464,7 +474,7 @@ sfc_status batch_encode(const float* xyz, int64_t n, int enc, const BatchSeg* se
                         uint32_t* idx, cudaStream_t s);
 // LSD radix sort on bits [begin_bit, end_bit) of the keys; the result ends in keys / vals
 sfc_status radix_sort_pairs_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                                 int begin_bit, int end_bit, cudaStream_t s, Scratch& scratch);
+                                 int begin_bit, int end_bit, cudaStream_t s, Scratch& scratch, unsigned int* fault);
 
 }  // namespace sfc
 

@@ -768,7 +768,7 @@ extern "C" sfc_status knn(sfc_octree h, const float* queries_xyz, int64_t n_quer
         SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaStreamSynchronize(s));
         if (hbad) return SFC_ERR_NOT_FINITE;
-        if (herr & sfc::kGuardTripped) return SFC_ERR_INTERNAL;
+        SFC_TRY(sfc::guard_status(herr));
     }
     return SFC_OK;
 }

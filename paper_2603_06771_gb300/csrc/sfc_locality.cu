@@ -105,7 +105,8 @@ __global__ void k_locality_mean(double* acc) {  // acc[0] = sum d, acc[1] = pair
 }
 
 // the position of every original point under `order` (nullptr: the input order)
-static sfc_status order_ranks(const Octree* t, int order, cudaStream_t s, Scratch& scratch, const uint32_t** rank) {
+static sfc_status order_ranks(const Octree* t, int order, cudaStream_t s, Scratch& scratch, const uint32_t** rank,
+                              unsigned int* fault) {
     *rank = nullptr;
     if (order == SFC_ENC_NONE) return SFC_OK;
     const int64_t n = t->n;
@@ -128,7 +129,7 @@ static sfc_status order_ranks(const Octree* t, int order, cudaStream_t s, Scratc
         else
             SFC_LAUNCH("locality_codes", s, k_order_codes<SFC_ENC_MORTON>, grid, 256, 0, t->pts, n, t->lo[0], t->lo[1],
                        t->lo[2], t->scale, k0, v0);
-        SFC_TRY(radix_sort_pairs(k0, v0, k1, v1, n, s, scratch));  // stable: equal codes by original index
+        SFC_TRY(radix_sort_pairs(k0, v0, k1, v1, n, s, scratch, fault));  // stable: equal codes by original index
         SFC_LAUNCH("locality_rank", s, k_invert_perm, grid, 256, 0, v0, n, r);
     }
     *rank = r;
@@ -172,7 +173,7 @@ sfc_status knn_locality(sfc_octree h, const int32_t* centre_ids, int64_t n_centr
                at, centre_ids, n_centres, t->n, q, bad);
     SFC_TRY(knn(h, q, n_centres, k, cuda_stream, nbr, d2));
     const uint32_t* rank = nullptr;
-    SFC_TRY(sfc::order_ranks(t, order, s, scratch, &rank));
+    SFC_TRY(sfc::order_ranks(t, order, s, scratch, &rank, bad));
     double* acc = nullptr;
     SFC_TRY(scratch.alloc(&acc, 5));
     SFC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * 5, s));
@@ -187,6 +188,7 @@ sfc_status knn_locality(sfc_octree h, const int32_t* centre_ids, int64_t n_centr
     SFC_CUDA(cudaMemcpyAsync(h_acc, acc, sizeof h_acc, cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
+    if (hbad & sfc::kWaitTimedOut) return SFC_ERR_TIMEOUT;
     if (hbad) return SFC_ERR_INVALID;
     const double pairs = h_acc[1];
     const double m2 = pairs > 0 ? h_acc[3] / pairs : 0.0, m3 = pairs > 0 ? h_acc[4] / pairs : 0.0;

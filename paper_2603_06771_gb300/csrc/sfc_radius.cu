@@ -756,7 +756,7 @@ static sfc_status count_impl(Octree* t, const float4* q4, int64_t rows, float r,
     SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
     if (hbad) return SFC_ERR_NOT_FINITE;
-    if (herr & kGuardTripped) return SFC_ERR_INTERNAL;
+    SFC_TRY(guard_status(herr));
     return SFC_OK;
 }
 
@@ -775,7 +775,7 @@ sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_
     SFC_CUDA(cudaMemcpyAsync(nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
-    return (herr & kGuardTripped) ? SFC_ERR_INTERNAL : SFC_OK;
+    return guard_status(herr);
 }
 
 static sfc_status fill_impl(Octree* t, const float4* q4, int64_t rows, float r, int kern, cudaStream_t s,
@@ -807,7 +807,7 @@ static sfc_status check_guard(const Octree* t, cudaStream_t s) {
     unsigned int herr = 0;
     SFC_CUDA(cudaMemcpyAsync(&herr, &t->scal->bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));
-    return (herr & kGuardTripped) ? SFC_ERR_INTERNAL : SFC_OK;
+    return guard_status(herr);
 }
 
 static sfc_status prepare(const Octree* t, const float* queries, int64_t rows, cudaStream_t s, Scratch& scratch,

@@ -180,6 +180,33 @@ def test_radius_caller_centres(kern, enc):
     assert np.array_equal(rp2, rp) and np.array_equal(cols2, cols)
 
 
+@pytest.mark.parametrize("enc", ["morton", "hilbert"])
+@pytest.mark.parametrize("spread", [4, 16])
+def test_caller_centres_with_constant_code_digits(spread, enc):
+    """Caller centres whose codes share most 8-bit digits: the sort of the centres skips
+    those passes (one pass left for spread 4, two for spread 16 under Morton, so the
+    sorted pairs end in either buffer), and the rows must still be the oracle's."""
+    side = float(1 << 21)
+    xyz = synth.uniform_cube(20_000, 107) * side
+    xyz = np.concatenate([xyz, [[0.0, 0.0, 0.0], [side, side, side]]]).astype(np.float32)  # scale 1
+    rng = synth.Rng(9)
+    cells = (1 << 20) + 256 * (rng.u64(0, 3 * 3000) % np.uint64(spread)).astype(np.int64).reshape(-1, 3)
+    if enc == "morton":
+        codes = oracle.encode_cells(cells.astype(np.uint32), ENC[enc])
+        varying = [d for d in range(8) if len(np.unique((codes >> np.uint64(8 * d)) & np.uint64(255))) > 1]
+        assert varying == ([3] if spread == 4 else [3, 4])
+    q = cells.astype(np.float32)
+    p = oracle.Pipeline(xyz, ENC[enc], 16)
+    orp, ocol = p.tree.radius(q, 60_000.0, KERN["sphere"])
+    t = sfc.octree_build(dev(xyz), enc, leaf_capacity=16)
+    assert t.scale == 1.0 and t.lo == (0.0, 0.0, 0.0)
+    rp, cols = gpu_csr(*sfc.radius_search(t, dev(q), 60_000.0, "sphere"))
+    assert orp[-1] > 0
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(cols, p.rows_by_rank(orp, ocol))
+    t.free()
+
+
 def test_radius_special_radii():
     xyz = cloud("uniform4097")
     t = sfc.octree_build(dev(xyz), "hilbert", leaf_capacity=16)
