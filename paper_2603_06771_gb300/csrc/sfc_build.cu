@@ -39,33 +39,72 @@ __global__ void k_bbox_init(BuildScalars* sc) {
     sc->ext = 1.0f;
 }
 
-__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ xyz, int64_t n, BuildScalars* sc) {
+// Four points at a time: three float4 loads hold x, y, z of four consecutive points (the
+// caller's array must be 16-byte aligned for these); point j of the four is p[3j .. 3j+2].
+__device__ __forceinline__ void load_four_points(const float* __restrict__ xyz, int64_t q, float p[12]) {
+    const float4* v = reinterpret_cast<const float4*>(xyz) + 3 * q;
+    const float4 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2);
+    p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w;
+    p[4] = b.x; p[5] = b.y; p[6] = b.z; p[7] = b.w;
+    p[8] = c.x; p[9] = c.y; p[10] = c.z; p[11] = c.w;
+}
+
+__device__ __forceinline__ void bbox_take(float v, int a, unsigned int mn[3], unsigned int mx[3], unsigned int& bad) {
+    if (!isfinite(v)) bad = 1u;
+    const unsigned int o = float_to_ordered(v);
+    mn[a] = min(mn[a], o);
+    mx[a] = max(mx[a], o);
+}
+
+// vec: xyz is 16-byte aligned (whole groups of four points by vector loads, the rest singly)
+__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ xyz, int64_t n, BuildScalars* sc, int vec) {
+    __shared__ unsigned int part[8][7];
     unsigned int mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu};
     unsigned int mx[3] = {0u, 0u, 0u};
     unsigned int bad = 0u;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t done = 0;
+    if (vec) {
+        const int64_t nq = n / 4;
+        for (int64_t q = tid; q < nq; q += stride) {
+            float p[12];
+            load_four_points(xyz, q, p);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float v = xyz[3 * i + a];
-            if (!isfinite(v)) bad = 1u;
-            const unsigned int o = float_to_ordered(v);
-            mn[a] = min(mn[a], o);
-            mx[a] = max(mx[a], o);
+            for (int j = 0; j < 12; ++j) bbox_take(p[j], j % 3, mn, mx, bad);
         }
+        done = 4 * nq;
     }
+    for (int64_t i = done + tid; i < n; i += stride) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) bbox_take(xyz[3 * i + a], a, mn, mx, bad);
+    }
+    // warp, then block, then one atomic per quantity and block
+    const unsigned int lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         mn[a] = __reduce_min_sync(0xffffffffu, mn[a]);
         mx[a] = __reduce_max_sync(0xffffffffu, mx[a]);
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
-    if (lane_id() == 0) {
+    if (lane == 0) {
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&sc->mn[a], mn[a]);
-            atomicMax(&sc->mx[a], mx[a]);
+            part[warp][a] = mn[a];
+            part[warp][3 + a] = mx[a];
         }
-        if (bad) atomicOr(&sc->bad, 1u);
+        part[warp][6] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        const int w_n = static_cast<int>(blockDim.x >> 5);
+        unsigned int v = part[0][threadIdx.x];
+        for (int w = 1; w < w_n; ++w) {
+            const unsigned int u = part[w][threadIdx.x];
+            v = threadIdx.x < 3 ? min(v, u) : (threadIdx.x < 6 ? max(v, u) : (v | u));
+        }
+        if (threadIdx.x < 3) atomicMin(&sc->mn[threadIdx.x], v);
+        else if (threadIdx.x < 6) atomicMax(&sc->mx[threadIdx.x - 3], v);
+        else if (v) atomicOr(&sc->bad, 1u);
     }
 }
 
@@ -86,21 +125,42 @@ __global__ void k_bbox_finish(BuildScalars* sc) {
 
 // ---------------------------------------------------------------------------------
 template <int ENC>
+__device__ __forceinline__ uint64_t code_of(float x, float y, float z, float lx, float ly, float lz, float s,
+                                            const HilbertTables& table) {
+    const uint32_t cx = cell_of(x, lx, s), cy = cell_of(y, ly, s), cz = cell_of(z, lz, s);
+    return ENC == SFC_ENC_HILBERT ? hilbert_code(cx, cy, cz, table) : morton_code(cx, cy, cz);
+}
+
+// vec: xyz, keys and idx are 16-byte aligned (groups of four points by vector loads and
+// stores, the rest singly)
+template <int ENC>
 __global__ void __launch_bounds__(256) k_encode(const float* __restrict__ xyz, int64_t n,
                                                 const BuildScalars* __restrict__ sc, uint64_t* __restrict__ keys,
-                                                uint32_t* __restrict__ idx) {
-    __shared__ uint16_t table[kHilbertTable];
-    if (ENC == SFC_ENC_HILBERT) {
-        fill_hilbert_table(table);
-        __syncthreads();
-    }
+                                                uint32_t* __restrict__ idx, int vec) {
+    __shared__ HilbertTables table;
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_tables(table);
     const float lx = sc->lo[0], ly = sc->lo[1], lz = sc->lo[2], s = sc->scale;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t cx = cell_of(xyz[3 * i], lx, s);
-        const uint32_t cy = cell_of(xyz[3 * i + 1], ly, s);
-        const uint32_t cz = cell_of(xyz[3 * i + 2], lz, s);
-        keys[i] = ENC == SFC_ENC_HILBERT ? hilbert_code(cx, cy, cz, table) : morton_code(cx, cy, cz);
+    int64_t done = 0;
+    if (vec) {
+        const int64_t nq = n / 4;
+        for (int64_t q = tid; q < nq; q += stride) {
+            float p[12];
+            load_four_points(xyz, q, p);
+            uint64_t k[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = code_of<ENC>(p[3 * j], p[3 * j + 1], p[3 * j + 2], lx, ly, lz, s, table);
+            ulonglong2* kv = reinterpret_cast<ulonglong2*>(keys) + 2 * q;
+            kv[0] = make_ulonglong2(k[0], k[1]);
+            kv[1] = make_ulonglong2(k[2], k[3]);
+            const uint32_t i0 = static_cast<uint32_t>(4 * q);
+            reinterpret_cast<uint4*>(idx)[q] = make_uint4(i0, i0 + 1, i0 + 2, i0 + 3);
+        }
+        done = 4 * nq;
+    }
+    for (int64_t i = done + tid; i < n; i += stride) {
+        keys[i] = code_of<ENC>(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lx, ly, lz, s, table);
         idx[i] = static_cast<uint32_t>(i);
     }
 }
@@ -108,11 +168,8 @@ __global__ void __launch_bounds__(256) k_encode(const float* __restrict__ xyz, i
 template <int ENC>
 __global__ void __launch_bounds__(256) k_encode_cells(const uint32_t* __restrict__ cells, int64_t n,
                                                       uint64_t* __restrict__ keys) {
-    __shared__ uint16_t table[kHilbertTable];
-    if (ENC == SFC_ENC_HILBERT) {
-        fill_hilbert_table(table);
-        __syncthreads();
-    }
+    __shared__ HilbertTables table;
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_tables(table);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t cx = cells[3 * i] & kCellMax, cy = cells[3 * i + 1] & kCellMax, cz = cells[3 * i + 2] & kCellMax;
@@ -125,9 +182,9 @@ template <int ENC>
 __global__ void __launch_bounds__(256) k_batch_encode(const float* __restrict__ xyz, int64_t n,
                                                       const BatchSeg* __restrict__ segs, int nsegs,
                                                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
-    __shared__ uint16_t table[kHilbertTable];
+    __shared__ HilbertTables table;
     __shared__ int64_t p0s[kBatchMax];
-    if (ENC == SFC_ENC_HILBERT) fill_hilbert_table(table);
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_tables(table);
     for (int i = threadIdx.x; i < nsegs; i += blockDim.x) p0s[i] = segs[i].p0;
     __syncthreads();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -362,11 +419,8 @@ template <int ENC>
 __global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ q, int64_t nq,
                                                      const BuildScalars* __restrict__ sc, uint64_t* __restrict__ keys,
                                                      uint32_t* __restrict__ idx, unsigned int* bad) {
-    __shared__ uint16_t table[kHilbertTable];
-    if (ENC == SFC_ENC_HILBERT) {
-        fill_hilbert_table(table);
-        __syncthreads();
-    }
+    __shared__ HilbertTables table;
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_tables(table);
     const float lx = sc->lo[0], ly = sc->lo[1], lz = sc->lo[2], s = sc->scale;
     unsigned int b = 0u;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -440,16 +494,17 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
     int64_t n_int = 0;
     if (n > 0) {
         // section 4: box, scale and codes
-        SFC_LAUNCH("bbox", s, k_bbox, grid, 256, 0, xyz, n, t->scal);
+        const int vec = (aligned16(xyz) && aligned16(t->keys) && aligned16(t->perm)) ? 1 : 0;
+        SFC_LAUNCH("bbox", s, k_bbox, grid, 256, 0, xyz, n, t->scal, vec);
         SFC_LAUNCH("bbox_finish", s, k_bbox_finish, 1, 1, 0, t->scal);
         uint64_t* keys_alt;
         uint32_t* perm_alt;
         SFC_TRY(scratch.alloc(&keys_alt, n));
         SFC_TRY(scratch.alloc(&perm_alt, n));
         if (t->enc == SFC_ENC_HILBERT)
-            SFC_LAUNCH("encode", s, k_encode<SFC_ENC_HILBERT>, grid, 256, 0, xyz, n, t->scal, t->keys, t->perm);
+            SFC_LAUNCH("encode", s, k_encode<SFC_ENC_HILBERT>, grid, 256, 0, xyz, n, t->scal, t->keys, t->perm, vec);
         else
-            SFC_LAUNCH("encode", s, k_encode<SFC_ENC_MORTON>, grid, 256, 0, xyz, n, t->scal, t->keys, t->perm);
+            SFC_LAUNCH("encode", s, k_encode<SFC_ENC_MORTON>, grid, 256, 0, xyz, n, t->scal, t->keys, t->perm, vec);
         // section 4: ascending codes, ties in input order
         SFC_TRY(radix_sort_pairs(t->keys, t->perm, keys_alt, perm_alt, n, s, scratch, &t->scal->bad));
         if (t->enc == SFC_ENC_NONE)

@@ -254,6 +254,8 @@ inline sfc_status guard_status(unsigned int bad) {
     return SFC_OK;
 }
 
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 inline unsigned int grid_for(int64_t n, int threads, int64_t cap = 1 << 30) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -438,15 +440,42 @@ __device__ inline void fill_hilbert_table(uint16_t* table) {
     }
 }
 
-__device__ __forceinline__ uint64_t hilbert_code(uint32_t x, uint32_t y, uint32_t z, const uint16_t* table) {
-    uint32_t state = 0;
-    uint64_t code = 0;
+// Two levels per lookup: entry (state, 3 input bits of a level then 3 of the level below)
+// = the two levels' 6 code bits | the state after both << 6, composed from the one-level
+// table.  Both tables live in shared memory, filled by every block.
+constexpr int kHilbertTable2 = kHilbertStates * 64;
+struct HilbertTables {
+    uint16_t one[kHilbertTable];
+    uint16_t two[kHilbertTable2];
+};
+
+// Called by every thread of the block (it synchronises the block).
+__device__ inline void fill_hilbert_tables(HilbertTables& t) {
+    fill_hilbert_table(t.one);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHilbertTable2; i += blockDim.x) {
+        const uint32_t e1 = t.one[(i >> 6) * 8 + ((i >> 3) & 7)];
+        const uint32_t e2 = t.one[(e1 >> 3) * 8 + (i & 7)];
+        t.two[i] = static_cast<uint16_t>(((e1 & 7u) << 3) | (e2 & 7u) | ((e2 >> 3) << 6));
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t level_bits(uint32_t x, uint32_t y, uint32_t z, int l) {
+    return (((x >> l) & 1u) << 2) | (((y >> l) & 1u) << 1) | ((z >> l) & 1u);
+}
+
+// The code of a cell: the top level alone, then the other 20 two at a time.
+__device__ __forceinline__ uint64_t hilbert_code(uint32_t x, uint32_t y, uint32_t z, const HilbertTables& t) {
+    static_assert(kLevels % 2 == 1, "one level alone, then pairs");
+    const uint32_t e0 = t.one[level_bits(x, y, z, kLevels - 1)];
+    uint64_t code = e0 & 7u;
+    uint32_t state = e0 >> 3;
 #pragma unroll
-    for (int l = kLevels - 1; l >= 0; --l) {
-        const uint32_t in = (((x >> l) & 1u) << 2) | (((y >> l) & 1u) << 1) | ((z >> l) & 1u);
-        const uint32_t e = table[state * 8 + in];
-        code = (code << 3) | (e & 7u);
-        state = e >> 3;
+    for (int l = kLevels - 2; l >= 1; l -= 2) {
+        const uint32_t e = t.two[state * 64 + ((level_bits(x, y, z, l) << 3) | level_bits(x, y, z, l - 1))];
+        code = (code << 6) | (e & 63u);
+        state = e >> 6;
     }
     return code;
 }

@@ -45,11 +45,8 @@ template <int ENC>
 __global__ void __launch_bounds__(256) k_order_codes(const float4* __restrict__ pts, int64_t n, float lx, float ly,
                                                      float lz, float s, uint64_t* __restrict__ keys,
                                                      uint32_t* __restrict__ ids) {
-    __shared__ uint16_t table[kHilbertTable];
-    if (ENC == SFC_ENC_HILBERT) {
-        fill_hilbert_table(table);
-        __syncthreads();
-    }
+    __shared__ HilbertTables table;
+    if (ENC == SFC_ENC_HILBERT) fill_hilbert_tables(table);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += stride) {
         const float4 q = pts[p];
