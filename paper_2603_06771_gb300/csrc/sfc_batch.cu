@@ -658,7 +658,7 @@ static sfc_status enqueue_order(const BatchTables& T, BatchBuffers& b, const flo
     SFC_LAUNCH("batch_gather", s, k_batch_gather, grid, 256, 0, xyz, n, b.codes, b.v0, b.segs, nsegs, b.k1, b.pts,
                b.perm);
     SFC_LAUNCH("batch_tree_count", s, k_batch_tree_count, grid, 256, 0, b.k1, n, b.segs, nsegs, b.cnt);
-    SFC_TRY(scan_u32_to_i64(b.cnt, b.first, n, s, tmp));
+    SFC_TRY(scan_u32_to_i64(b.cnt, b.first, n, s, tmp, b.err));
     SFC_LAUNCH("batch_seg_internal", s, k_batch_seg_internal, sgrid, 128, 0, b.segs, nsegs, b.first);
     SFC_LAUNCH("batch_layout", s, k_batch_layout, 1, 1024, 0, b.segs, nsegs, b.int_cap, b.node_cap, b.leaf_cap, b.table,
                b.table_cloud, static_cast<int>(T.table.size()), b.tot);
@@ -718,7 +718,7 @@ static sfc_status enqueue_radius_count(const BatchTables& T, BatchBuffers& b, in
                                     static_cast<int>(T.count[kern]), T.groups[kern], kern, false, b.counts, nullptr,
                                     nullptr, b.err, prune, records_of(T, b, kern), &b.tot->flags, kOverNodes | kNonFinite,
                                     s));
-    return scan_u32_to_i64(b.counts, row_ptr, T.n_total, s, tmp);
+    return scan_u32_to_i64(b.counts, row_ptr, T.n_total, s, tmp, b.err);
 }
 
 // The fill pass into cols (capacity cols_cap), then every cloud's row bounds.
@@ -969,7 +969,7 @@ static sfc_status timed_pass(const std::vector<sfc_batch_cloud>& clouds, const f
                                     kOverNodes | kNonFinite, s));
         SFC_TRY(ev.mark(&mc[kern][1]));
     }
-    SFC_TRY(scan_u32_to_i64(b.counts, row_ptr, n, s, tmp));
+    SFC_TRY(scan_u32_to_i64(b.counts, row_ptr, n, s, tmp, b.err));
     int64_t nnz = 0;
     SFC_CUDA(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof nnz, cudaMemcpyDeviceToHost, s));
     SFC_CUDA(cudaStreamSynchronize(s));

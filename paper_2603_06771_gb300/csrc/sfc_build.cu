@@ -517,7 +517,7 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
         SFC_TRY(scratch.alloc(&cnt, n));
         SFC_TRY(scratch.alloc(&first, n + 1));
         SFC_LAUNCH("tree_count", s, k_tree_count, grid, 256, 0, t->keys, n, static_cast<int64_t>(t->leaf_cap), cnt);
-        SFC_TRY(scan_u32_to_i64(cnt, first, n, s, scratch));
+        SFC_TRY(scan_u32_to_i64(cnt, first, n, s, scratch, &t->scal->bad));
         BuildScalars hs;
         SFC_CUDA(cudaMemcpyAsync(&n_int, first + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaMemcpyAsync(&hs, t->scal, sizeof(BuildScalars), cudaMemcpyDeviceToHost, s));

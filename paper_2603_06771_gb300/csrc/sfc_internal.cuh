@@ -199,13 +199,15 @@ sfc_status dev_alloc(T** p, size_t count, cudaStream_t s) {
 }
 void dev_free(void* p, cudaStream_t s);
 
-// Exclusive scans: out[0] = 0, out[i + 1] = out[i] + in[i], out has n + 1 entries.
-// in and out may alias (in-place) when they have the same type.
-sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
-sfc_status scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Scratch& scratch);
-// The same scan with the per-tile sums in a caller buffer of scan_tile_count(n) entries.
+// Exclusive scan: out[0] = 0, out[i + 1] = out[i] + in[i], out has n + 1 entries (one
+// kernel, tiles chained by a bounded decoupled look-back).  fault (device, may be null)
+// gets kWaitTimedOut if a wait gave up (the offsets are then wrong).
+sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch,
+                           unsigned int* fault = nullptr);
+// The same scan with its look-back words in a caller buffer of scan_tile_count(n) entries.
 int64_t scan_tile_count(int64_t n);
-sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s);
+sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s,
+                                    unsigned int* fault = nullptr);
 // All-points count pass of the radius search into caller buffers (counts: one entry per
 // point, tile_sums: scan_tile_count(n) entries); reads nnz back (one synchronisation).
 sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_t s, uint32_t* counts,

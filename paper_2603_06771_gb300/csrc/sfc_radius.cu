@@ -748,7 +748,7 @@ static sfc_status count_impl(Octree* t, const float4* q4, int64_t rows, float r,
             return st;
         }
         if (a.rec_mode == 1) t->records.valid = true;
-        SFC_TRY(scan_u32_to_i64(counts, row_ptr, rows, s, scratch));
+        SFC_TRY(scan_u32_to_i64(counts, row_ptr, rows, s, scratch, &t->scal->bad));
     }
     unsigned int hbad = 0, herr = 0;
     SFC_CUDA(cudaMemcpyAsync(nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -769,7 +769,7 @@ sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_
         RadiusArgs a = make_args(t, t->pts, rows, r);
         a.counts = counts;
         SFC_TRY(launch_search<false>(t, a, kern, s));
-        SFC_TRY(scan_u32_to_i64_presized(counts, row_ptr, rows, tile_sums, s));
+        SFC_TRY(scan_u32_to_i64_presized(counts, row_ptr, rows, tile_sums, s, &t->scal->bad));
     }
     unsigned int herr = 0;
     SFC_CUDA(cudaMemcpyAsync(nnz, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -167,8 +167,7 @@ void Scratch::release(const void* p) {
 void dev_free(void* p, cudaStream_t s) { raw_free(p, s); }
 
 // ---------------------------------------------------------------------------------
-// exclusive scan: tiles of kScanTile elements; per-tile sums, a single-block scan of
-// the tile sums, then each tile is scanned again with its offset added.
+// exclusive scans: tiles of kScanTile elements.
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -206,92 +205,133 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total) {
     return prefix + x - v;
 }
 
-template <typename TI, typename TO>
-__global__ void __launch_bounds__(kScanThreads) k_scan_tile_sums(const TI* __restrict__ in, int64_t n,
-                                                                 TO* __restrict__ sums) {
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
-    TO acc = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j)
-        if (base + j < n) acc += static_cast<TO>(in[base + j]);
-    TO total;
-    block_exclusive_scan<TO, kScanThreads>(acc, &total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+__device__ __forceinline__ void store_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <typename TO>
-__global__ void __launch_bounds__(1024) k_scan_spine(TO* __restrict__ sums, int64_t m) {
-    TO carry = 0;
-    for (int64_t base = 0; base < m; base += 1024) {
-        int64_t i = base + threadIdx.x;
-        TO v = i < m ? sums[i] : TO(0);
-        TO total;
-        TO ex = block_exclusive_scan<TO, 1024>(v, &total);
-        if (i < m) sums[i] = carry + ex;
-        carry += total;
-    }
+__device__ __forceinline__ uint64_t load_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-template <typename TI, typename TO>
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const TI* in, TO* out, int64_t n,
-                                                             const TO* __restrict__ sums) {
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
-    TO v[kScanItems];
-    TO acc = 0;
+// Exclusive scan of uint32 counts into int64 offsets (out[n] = the total) in one pass
+// (vec: in and out are 16-byte aligned, whole runs of 8 by vector loads and stores):
+// tiles of kScanTile elements take a ticket, scan themselves, publish their sum and learn
+// the sum of the tiles before them by decoupled look-back (D. Merrill and M. Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), one warp reading 32
+// earlier tiles' words at a time.  A tile only waits on tiles that are already running;
+// every wait is bounded all the same.
+// Look-back words (tiles of them, then the ticket counter): bit 63 the inclusive prefix
+// of this and all earlier tiles, bit 62 this tile's own sum, bits 61-0 the value.
+constexpr uint64_t kScanPrefix = 1ull << 63;
+constexpr uint64_t kScanSum = 1ull << 62;
+constexpr uint64_t kScanValue = (1ull << 62) - 1;
+constexpr int kScanSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        v[j] = base + j < n ? static_cast<TO>(in[base + j]) : TO(0);
-        acc += v[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ in, int64_t* __restrict__ out,
+                                                       int64_t n, uint64_t* __restrict__ look, int64_t tiles,
+                                                       unsigned int* fault, int vec) {
+    __shared__ uint32_t s_tile;
+    __shared__ int64_t s_before;
+    if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int*>(look + tiles), 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    static_assert(kScanItems % 4 == 0, "whole 16-byte loads and stores per thread");
+    uint32_t v[kScanItems];
+    const bool full = vec && base + kScanItems <= n;
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < kScanItems / 4; ++j) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(in + base) + j);
+            v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) v[j] = base + j < n ? in[base + j] : 0u;
     }
-    TO total;
-    TO run = block_exclusive_scan<TO, kScanThreads>(acc, &total) + sums[blockIdx.x];
+    int64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) acc += v[j];
+    int64_t total;
+    const int64_t ex = block_exclusive_scan<int64_t, kScanThreads>(acc, &total);
+    if (threadIdx.x < 32) {
+        const unsigned int lane = threadIdx.x;
+        if (lane == 0) store_relaxed(look + tile, (tile == 0 ? kScanPrefix : kScanSum) | static_cast<uint64_t>(total));
+        int64_t before = 0;
+        int spins = 0;
+        for (int64_t j = tile - 1; j >= 0;) {
+            // lane l reads tile j - l (the nearest first); before the first tile there is a prefix of 0
+            const uint64_t w = j - static_cast<int64_t>(lane) >= 0 ? load_relaxed(look + j - lane) : kScanPrefix;
+            const unsigned int ready = __ballot_sync(0xffffffffu, (w >> 62) != 0);
+            const unsigned int prefix = __ballot_sync(0xffffffffu, (w >> 63) != 0);
+            const int first_prefix = prefix ? __ffs(prefix) - 1 : 32;
+            const int first_missing = ~ready ? __ffs(~ready) - 1 : 32;
+            const int use = min(first_missing, first_prefix + 1);  // words added this round
+            before += warp_sum_i64(static_cast<int>(lane) < use ? static_cast<int64_t>(w & kScanValue) : 0);
+            if (first_prefix < first_missing) break;  // reached an inclusive prefix
+            j -= use;
+            if (first_missing < 32) {
+                if (++spins > kScanSpinLimit) {  // never expected: the tiles before are running
+                    if (fault && lane == 0) atomicOr(fault, kWaitTimedOut);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (lane == 0) {
+            if (tile > 0) store_relaxed(look + tile, kScanPrefix | static_cast<uint64_t>(before + total));
+            s_before = before;
+        }
+    }
+    __syncthreads();
+    int64_t run = s_before + ex;
+    int64_t o[kScanItems];
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        if (base + j < n) out[base + j] = run;
+        o[j] = run;
         run += v[j];
     }
-    // the element one past the end receives the grand total
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[blockIdx.x] + total;
-}
-
-template <typename TI, typename TO>
-static sfc_status scan_impl(const TI* in, TO* out, int64_t n, cudaStream_t s, Scratch& scratch) {
-    if (n == 0) {
-        SFC_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), s));
-        return SFC_OK;
+    if (full) {
+        longlong2* d = reinterpret_cast<longlong2*>(out + base);
+#pragma unroll
+        for (int j = 0; j < kScanItems / 2; ++j) d[j] = make_longlong2(o[2 * j], o[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (base + j < n) out[base + j] = o[j];
     }
-    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    TO* sums = nullptr;
-    SFC_TRY(scratch.alloc(&sums, static_cast<size_t>(tiles)));
-    SFC_LAUNCH("scan_tile_sums", s, (k_scan_tile_sums<TI, TO>), static_cast<unsigned int>(tiles), kScanThreads, 0,
-               in, n, sums);
-    SFC_LAUNCH("scan_spine", s, k_scan_spine<TO>, 1, 1024, 0, sums, tiles);
-    SFC_LAUNCH("scan_apply", s, (k_scan_apply<TI, TO>), static_cast<unsigned int>(tiles), kScanThreads, 0, in, out,
-               n, sums);
-    return SFC_OK;
+    // the element one past the end receives the grand total
+    if (tile == tiles - 1 && threadIdx.x == 0) out[n] = s_before + total;
 }
 
-sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch) {
-    return scan_impl<uint32_t, int64_t>(in, out, n, s, scratch);
-}
-sfc_status scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Scratch& scratch) {
-    return scan_impl<uint32_t, uint32_t>(in, out, n, s, scratch);
-}
+int64_t scan_tile_count(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-int64_t scan_tile_count(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
-
-sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s) {
+sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s,
+                                    unsigned int* fault) {
     if (n == 0) {
         SFC_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return SFC_OK;
     }
-    const int64_t tiles = scan_tile_count(n);
-    SFC_LAUNCH("scan_tile_sums", s, (k_scan_tile_sums<uint32_t, int64_t>), static_cast<unsigned int>(tiles),
-               kScanThreads, 0, in, n, tile_sums);
-    SFC_LAUNCH("scan_spine", s, k_scan_spine<int64_t>, 1, 1024, 0, tile_sums, tiles);
-    SFC_LAUNCH("scan_apply", s, (k_scan_apply<uint32_t, int64_t>), static_cast<unsigned int>(tiles), kScanThreads,
-               0, in, out, n, tile_sums);
+    const int64_t words = scan_tile_count(n);
+    SFC_CUDA(cudaMemsetAsync(tile_sums, 0, sizeof(int64_t) * words, s));
+    SFC_LAUNCH("scan", s, k_scan, static_cast<unsigned int>(words - 1), kScanThreads, 0, in, out, n,
+               reinterpret_cast<uint64_t*>(tile_sums), words - 1, fault, (aligned16(in) && aligned16(out)) ? 1 : 0);
     return SFC_OK;
+}
+
+sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch,
+                           unsigned int* fault) {
+    int64_t* look = nullptr;
+    if (n > 0) SFC_TRY(scratch.alloc(&look, static_cast<size_t>(scan_tile_count(n))));
+    return scan_u32_to_i64_presized(in, out, n, look, s, fault);
 }
 
 // ---------------------------------------------------------------------------------
@@ -338,15 +378,6 @@ constexpr uint64_t kLookValue = (1ull << 56) - 1;
 constexpr int kLookSpinLimit = 1 << 22;  // rounds that find a word not yet written before the wait gives up
 constexpr int kLookWindow = 4;           // look-back words read at once
 
-__device__ __forceinline__ void store_relaxed(uint64_t* p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t load_relaxed(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // Digit counts of every pass in one read of the keys (runs of equal digits in a thread's
 // keys are added at once, so sorted or clustered keys do not pile atomics on one counter);
