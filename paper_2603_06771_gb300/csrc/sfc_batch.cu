@@ -453,7 +453,7 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
                                int prune, const BatchRecords& rec, const unsigned int* skip, unsigned int skip_mask,
                                cudaStream_t s);
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, bool exact,
                             int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
                             unsigned int skip_mask, cudaStream_t s);
 
@@ -485,6 +485,7 @@ struct BatchTables {
     int64_t knn_total = 0;
     int64_t rec_groups = 0;  // warp groups of the radius launches
     int rec_cap[kLaunchSets] = {0, 0, 0, 0, 0, 0, 0, 0};  // record slots per group of each radius launch
+    bool knn_exact[kLaunchSets] = {true, true, true, true, true, true, true, true};  // every k equals the class's
     int64_t rec_slots = 0;   // record slots of all radius launches
     int64_t int_bound = 0;   // internal nodes of all clouds at most
 };
@@ -529,6 +530,7 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
                 T.out0[i] = T.knn_total;
                 T.knn_total += c.n_points * c.k;
                 const int b = 4 + (c.k <= 8 ? 0 : (c.k <= 16 ? 1 : (c.k <= 32 ? 2 : 3)));
+                if (c.k != (8 << (b - 4))) T.knn_exact[b] = false;
                 sets[b].push_back(q);
                 set_cloud[b].push_back(i);
             }
@@ -704,8 +706,8 @@ static sfc_status enqueue_knn(const BatchTables& T, BatchBuffers& b, int32_t* kn
     const int kmax_of[4] = {8, 16, 32, 64};
     for (int t = 4; t < kLaunchSets; ++t)
         SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
-                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], 0, knn_idx, knn_d2,
-                                 b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.knn_exact[t], knn_idx,
+                                 knn_d2, b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
     return SFC_OK;
 }
 
@@ -952,8 +954,8 @@ static sfc_status timed_pass(const std::vector<sfc_batch_cloud>& clouds, const f
     for (int t = 4; t < kLaunchSets; ++t) {
         SFC_TRY(ev.mark(&mk[t][0]));
         SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
-                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], 0, knn_idx, knn_d2, b.err,
-                                 &b.tot->flags, kOverNodes | kNonFinite, s));
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.knn_exact[t], knn_idx,
+                                 knn_d2, b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
         SFC_TRY(ev.mark(&mk[t][1]));
     }
     int64_t* row_ptr = nullptr;

@@ -119,17 +119,28 @@ struct BestList {
 // levels of a long list (the four children of a level load together): kNN k = 50 on the
 // 10M tile 42.2 -> 36.9 ms; for k <= 16 the binary heap is as fast or faster (k = 8: 5.5
 // vs 5.9 ms).
-template <int D>
+// KFIX > 0: the list size is that compile-time constant (every loop over the slots and
+// every sift unrolls); 0: the size is k, known at run time.
+template <int D, int KFIX = 0>
 struct LaneHeap {
     static_assert(D == 2 || D == 4, "binary or 4-ary");
+    static_assert(KFIX <= kMaxK, "at most kMaxK pairs");
+    // levels a sift can move down in a list of at most kMaxK = 64 pairs, plus the last test
+    static constexpr int kSiftSteps = D == 2 ? 7 : 4;
     uint64_t* slot0;  // &heap[0][lane]
     uint64_t kth;     // register copy of the root
-    int k;
+    int k_;
+    __device__ __forceinline__ int size() const { return KFIX > 0 ? KFIX : k_; }
     __device__ __forceinline__ uint64_t& at(int s) const { return slot0[s * 32]; }
     __device__ __forceinline__ void init(uint64_t* base, int kk) {
         slot0 = base;
-        k = kk;
-        for (int s = 0; s < k; ++s) at(s) = kNoPair;
+        k_ = kk;
+        if constexpr (KFIX > 0) {
+#pragma unroll
+            for (int s = 0; s < KFIX; ++s) at(s) = kNoPair;
+        } else {
+            for (int s = 0; s < k_; ++s) at(s) = kNoPair;
+        }
         kth = kNoPair;
     }
     // the largest of the children c0 .. c0 + D - 1 (those below `size`; c0 < size) and its slot
@@ -160,7 +171,8 @@ struct LaneHeap {
     }
     // place x at slot pos of the heap of the first `size` slots and restore the order below it
     __device__ __forceinline__ void sift_down(uint64_t x, int size, int pos = 0) {
-        for (;;) {
+#pragma unroll
+        for (int step = 0; step < kSiftSteps; ++step) {
             const int c0 = D * pos + 1;
             if (c0 >= size) break;
             int c;
@@ -174,13 +186,13 @@ struct LaneHeap {
     // replace the root (the k-th pair) by nk < kth; the new root, the larger of nk and the
     // root's largest child, is known before the rest of the sift and stays in a register
     __device__ __forceinline__ void insert(uint64_t nk) {
-        if (k > 1) {
+        if (size() > 1) {
             int c;
-            const uint64_t cv = max_child(1, k, &c);
+            const uint64_t cv = max_child(1, size(), &c);
             if (cv > nk) {
                 at(0) = cv;
                 kth = cv;
-                sift_down(nk, k, c);
+                sift_down(nk, size(), c);
                 return;
             }
         }
@@ -189,11 +201,11 @@ struct LaneHeap {
     }
     // the k slots hold arbitrary pairs: restore the heap order bottom-up
     __device__ __forceinline__ void heapify() {
-        for (int i = (k - 2) / D; i >= 0; --i) sift_down(at(i), k, i);
+        for (int i = (size() - 2) / D; i >= 0; --i) sift_down(at(i), size(), i);
         kth = at(0);
     }
     __device__ __forceinline__ void finish() {
-        for (int end = k - 1; end > 0; --end) {
+        for (int end = size() - 1; end > 0; --end) {
             const uint64_t top = at(0);
             const uint64_t last = at(end);
             at(end) = top;
@@ -202,7 +214,7 @@ struct LaneHeap {
     }
     __device__ __forceinline__ float kth_d2() const { return __uint_as_float(static_cast<uint32_t>(kth >> 32)); }
     __device__ __forceinline__ void store(const KnnArgs& a, int64_t base) const {
-        for (int s = 0; s < k; ++s) {
+        for (int s = 0; s < size(); ++s) {
             const uint64_t key = at(s);
             const uint32_t id = static_cast<uint32_t>(key);
             a.out_idx[base + s] = id == kNoIndex ? -1 : static_cast<int32_t>(id);
@@ -278,7 +290,9 @@ __host__ __device__ constexpr int knn_warps() { return kKnnWarps; }
 // them there.  Per chunk, pass 1 marks the points that beat each lane's current k-th pair
 // and pass 2 lets each lane insert its marked points.
 // STATS: also accumulate the work counters of sfc_search_stats.
-template <int KMAX, bool STATS = false>
+// KFIX: every list has exactly KFIX pairs; WFIX: the seeding window is WFIX positions per
+// side (compile-time sizes, so the list and window loops unroll; batches pass 0 for both).
+template <int KMAX, bool STATS = false, int KFIX = 0, int WFIX = 0>
 // the minimum resident blocks match what shared memory allows for each list size: with
 // 8-byte stack entries 32 one-warp blocks fit for k <= 16 at 64 registers (k = 16 on the
 // 10M-point tile: 9.51 ms at 26 resident blocks, 9.10 ms at 32)
@@ -298,8 +312,8 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 16 ? 32 : (KMA
     const int64_t group = static_cast<int64_t>(blockIdx.x) * kWarps + warp;
     int64_t first = group * 32, q_lo = 0, q_end = a.nq, out0 = 0;
     int32_t root = 0;
-    int k = a.k;
-    int64_t window = a.window;
+    int k = KFIX > 0 ? KFIX : a.k;
+    int64_t window = WFIX > 0 ? WFIX : a.window;
     unsigned int gsize = 32;  // centres of this group (batched clouds may ask for fewer)
     if (a.segs) {
         if (group >= a.ngroups) return;
@@ -311,8 +325,8 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 16 ? 32 : (KMA
         q_end = sg.q0 + sg.nq;
         out0 = sg.row0;
         root = sg.root;
-        k = sg.k;
-        window = sg.window;
+        if constexpr (KFIX == 0) k = sg.k;  // else every cloud's k is KFIX
+        if constexpr (WFIX == 0) window = sg.window;
     } else if (first >= a.nq) {
         return;
     }
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(knn_warps<KMAX>() * 32, KMAX <= 16 ? 32 : (KMA
         st.zero();
         st.v[kStWalks] = lane == 0;
     }
-    LaneHeap<(KMAX >= 32 ? 4 : 2)> best;
+    LaneHeap<(KMAX >= 32 ? 4 : 2), KFIX> best;
     best.init(&heaps[warp][0][lane], k);
     auto key_of = [&](const float4& q) {
         return pair_key(sq_dist(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z)), __float_as_uint(q.w));
@@ -646,6 +660,23 @@ __global__ void __launch_bounds__(128) k_knn_lane(KnnArgs a) {
     }
 }
 
+// Lists of exactly KF pairs (and, for all-points searches, a window of KF positions per
+// side) run a copy of the group kernel with those sizes fixed at compile time: the list and
+// window loops unroll (kNN on the 10M-point tile: k = 16 8.85 -> 8.15 ms, k = 8 5.12 ->
+// 4.85 ms).  *done: k is KF and the kernel was launched.
+template <int KMAX, int KF>
+static sfc_status launch_knn_fixed(const KnnArgs& a, cudaStream_t s, bool* done) {
+    static_assert(KF <= KMAX, "the list fits the kernel's shared memory");
+    constexpr int kWarps = knn_warps<KMAX>();
+    *done = a.k == KF;
+    if (!*done) return SFC_OK;
+    if (a.window == KF)
+        SFC_LAUNCH("knn", s, (k_knn_group<KMAX, false, KF, KF>), grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
+    else
+        SFC_LAUNCH("knn", s, (k_knn_group<KMAX, false, KF>), grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
+    return SFC_OK;
+}
+
 template <int KMAX>
 static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) {
     constexpr int kWarps = knn_warps<KMAX>();
@@ -655,6 +686,11 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
     } else if (t->enc == SFC_ENC_NONE) {
         SFC_LAUNCH("knn", s, k_knn_lane<KMAX>, grid_for(a.nq, 128), 128, 0, a);
     } else {
+        bool done = false;
+        SFC_TRY((launch_knn_fixed<KMAX, KMAX>(a, s, &done)));
+        if constexpr (KMAX == 64)  // k = 50 of the LiDAR kNN workloads
+            if (!done) SFC_TRY((launch_knn_fixed<KMAX, 50>(a, s, &done)));
+        if (done) return SFC_OK;
         SFC_LAUNCH("knn", s, k_knn_group<KMAX>, grid_for(a.ngroups, kWarps), kWarps * 32, 0, a);
     }
     return SFC_OK;
@@ -662,7 +698,7 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
 
 // all kNN clouds of one list-size class of a batch, in one launch (sfc_batch.cu)
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int window,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, bool exact,
                             int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
                             unsigned int skip_mask, cudaStream_t s) {
     if (ngroups == 0) return SFC_OK;
@@ -679,18 +715,31 @@ sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeB
     a.out_d2 = out_d2;
     a.err = err;
     a.max_steps = total_nodes;
-    a.window = window;
+    a.window = 0;  // each cloud's own
     a.segs = segs;
     a.nsegs = nsegs;
     a.ngroups = ngroups;
     a.skip = skip;
     a.skip_mask = skip_mask;
     const unsigned int grid = grid_for(ngroups, kKnnWarps);
+    // exact: every cloud's k is kmax, so the lists have a compile-time size
     switch (kmax) {
-    case 8: SFC_LAUNCH("batch_knn", s, k_knn_group<8>, grid, kKnnWarps * 32, 0, a); break;
-    case 16: SFC_LAUNCH("batch_knn", s, k_knn_group<16>, grid, kKnnWarps * 32, 0, a); break;
-    case 32: SFC_LAUNCH("batch_knn", s, k_knn_group<32>, grid, kKnnWarps * 32, 0, a); break;
-    default: SFC_LAUNCH("batch_knn", s, k_knn_group<64>, grid, kKnnWarps * 32, 0, a); break;
+    case 8:
+        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<8, false, 8>), grid, kKnnWarps * 32, 0, a);
+        else SFC_LAUNCH("batch_knn", s, k_knn_group<8>, grid, kKnnWarps * 32, 0, a);
+        break;
+    case 16:
+        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<16, false, 16>), grid, kKnnWarps * 32, 0, a);
+        else SFC_LAUNCH("batch_knn", s, k_knn_group<16>, grid, kKnnWarps * 32, 0, a);
+        break;
+    case 32:
+        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<32, false, 32>), grid, kKnnWarps * 32, 0, a);
+        else SFC_LAUNCH("batch_knn", s, k_knn_group<32>, grid, kKnnWarps * 32, 0, a);
+        break;
+    default:
+        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<64, false, 64>), grid, kKnnWarps * 32, 0, a);
+        else SFC_LAUNCH("batch_knn", s, k_knn_group<64>, grid, kKnnWarps * 32, 0, a);
+        break;
     }
     return SFC_OK;
 }
