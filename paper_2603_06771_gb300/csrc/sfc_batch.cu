@@ -453,7 +453,7 @@ sfc_status batch_radius_launch(const float4* pts, const uint32_t* perm, const No
                                int prune, const BatchRecords& rec, const unsigned int* skip, unsigned int skip_mask,
                                cudaStream_t s);
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, bool exact,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int exact,
                             int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
                             unsigned int skip_mask, cudaStream_t s);
 
@@ -486,6 +486,7 @@ struct BatchTables {
     int64_t rec_groups = 0;  // warp groups of the radius launches
     int rec_cap[kLaunchSets] = {0, 0, 0, 0, 0, 0, 0, 0};  // record slots per group of each radius launch
     bool knn_exact[kLaunchSets] = {true, true, true, true, true, true, true, true};  // every k equals the class's
+    bool knn_wexact[kLaunchSets] = {true, true, true, true, true, true, true, true};  // and every seeding window
     int64_t rec_slots = 0;   // record slots of all radius launches
     int64_t int_bound = 0;   // internal nodes of all clouds at most
 };
@@ -531,6 +532,7 @@ static void make_tables(const sfc_batch_cloud* clouds, int n_clouds, int ncap, B
                 T.knn_total += c.n_points * c.k;
                 const int b = 4 + (c.k <= 8 ? 0 : (c.k <= 16 ? 1 : (c.k <= 32 ? 2 : 3)));
                 if (c.k != (8 << (b - 4))) T.knn_exact[b] = false;
+                if (q.window != (8 << (b - 4))) T.knn_wexact[b] = false;
                 sets[b].push_back(q);
                 set_cloud[b].push_back(i);
             }
@@ -706,7 +708,8 @@ static sfc_status enqueue_knn(const BatchTables& T, BatchBuffers& b, int32_t* kn
     const int kmax_of[4] = {8, 16, 32, 64};
     for (int t = 4; t < kLaunchSets; ++t)
         SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
-                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.knn_exact[t], knn_idx,
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4],
+                                 T.knn_exact[t] ? (T.knn_wexact[t] ? 2 : 1) : 0, knn_idx,
                                  knn_d2, b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
     return SFC_OK;
 }
@@ -954,7 +957,8 @@ static sfc_status timed_pass(const std::vector<sfc_batch_cloud>& clouds, const f
     for (int t = 4; t < kLaunchSets; ++t) {
         SFC_TRY(ev.mark(&mk[t][0]));
         SFC_TRY(batch_knn_launch(b.pts, b.perm, b.nodes, b.child, b.node_cap, b.table + T.off[t],
-                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4], T.knn_exact[t], knn_idx,
+                                 static_cast<int>(T.count[t]), T.groups[t], kmax_of[t - 4],
+                                 T.knn_exact[t] ? (T.knn_wexact[t] ? 2 : 1) : 0, knn_idx,
                                  knn_d2, b.err, &b.tot->flags, kOverNodes | kNonFinite, s));
         SFC_TRY(ev.mark(&mk[t][1]));
     }

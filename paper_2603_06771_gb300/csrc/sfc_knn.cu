@@ -696,9 +696,17 @@ static sfc_status launch_knn(const Octree* t, const KnnArgs& a, cudaStream_t s) 
     return SFC_OK;
 }
 
+template <int KMAX>
+static sfc_status launch_batch_knn(const KnnArgs& a, unsigned int grid, int exact, cudaStream_t s) {
+    if (exact == 2) SFC_LAUNCH("batch_knn", s, (k_knn_group<KMAX, false, KMAX, KMAX>), grid, kKnnWarps * 32, 0, a);
+    else if (exact == 1) SFC_LAUNCH("batch_knn", s, (k_knn_group<KMAX, false, KMAX>), grid, kKnnWarps * 32, 0, a);
+    else SFC_LAUNCH("batch_knn", s, k_knn_group<KMAX>, grid, kKnnWarps * 32, 0, a);
+    return SFC_OK;
+}
+
 // all kNN clouds of one list-size class of a batch, in one launch (sfc_batch.cu)
 sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeBox* nodes, const int32_t* child,
-                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, bool exact,
+                            int64_t total_nodes, const SearchSeg* segs, int nsegs, int64_t ngroups, int kmax, int exact,
                             int32_t* out_idx, float* out_d2, unsigned int* err, const unsigned int* skip,
                             unsigned int skip_mask, cudaStream_t s) {
     if (ngroups == 0) return SFC_OK;
@@ -722,24 +730,13 @@ sfc_status batch_knn_launch(const float4* pts, const uint32_t* perm, const NodeB
     a.skip = skip;
     a.skip_mask = skip_mask;
     const unsigned int grid = grid_for(ngroups, kKnnWarps);
-    // exact: every cloud's k is kmax, so the lists have a compile-time size
+    // exact 1: every cloud's k is kmax, so the lists have a compile-time size; 2: every
+    // seeding window is kmax positions per side as well
     switch (kmax) {
-    case 8:
-        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<8, false, 8>), grid, kKnnWarps * 32, 0, a);
-        else SFC_LAUNCH("batch_knn", s, k_knn_group<8>, grid, kKnnWarps * 32, 0, a);
-        break;
-    case 16:
-        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<16, false, 16>), grid, kKnnWarps * 32, 0, a);
-        else SFC_LAUNCH("batch_knn", s, k_knn_group<16>, grid, kKnnWarps * 32, 0, a);
-        break;
-    case 32:
-        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<32, false, 32>), grid, kKnnWarps * 32, 0, a);
-        else SFC_LAUNCH("batch_knn", s, k_knn_group<32>, grid, kKnnWarps * 32, 0, a);
-        break;
-    default:
-        if (exact) SFC_LAUNCH("batch_knn", s, (k_knn_group<64, false, 64>), grid, kKnnWarps * 32, 0, a);
-        else SFC_LAUNCH("batch_knn", s, k_knn_group<64>, grid, kKnnWarps * 32, 0, a);
-        break;
+    case 8: SFC_TRY(launch_batch_knn<8>(a, grid, exact, s)); break;
+    case 16: SFC_TRY(launch_batch_knn<16>(a, grid, exact, s)); break;
+    case 32: SFC_TRY(launch_batch_knn<32>(a, grid, exact, s)); break;
+    default: SFC_TRY(launch_batch_knn<64>(a, grid, exact, s)); break;
     }
     return SFC_OK;
 }
