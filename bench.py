@@ -52,18 +52,18 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 190629888 + 1250618112, "sha256": "11d93c968d4290235f3fdf1c27cd76d5ebec6a03eeefa61045a25c295ced3138"},
-    "radius_fill": {"bytes_per_launch": 3166897408 + 4249998848, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
-    "radius_count": {"bytes_per_launch": 310978560 + 912199680, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "knn": {"bytes_per_launch": 190045440 + 1250285312, "sha256": "b41a0e699fd256738b13a9416afd50436e4f31b39af13e79e6264d9250a031b6"},
+    "radius_fill": {"bytes_per_launch": 3166582528 + 4249777920, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
+    "radius_count": {"bytes_per_launch": 309697024 + 912296448, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1551432897 / 62500, "sha256": "11d93c968d4290235f3fdf1c27cd76d5ebec6a03eeefa61045a25c295ced3138"},
-    "radius_count": {"warp_inst": 714693086 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
-    "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "186a6c218afde95040f08363ec2c6029cb6c0c909e48d71d1f4227c1eb38fe2c"},
+    "knn": {"warp_inst": 1368283468 / 62500, "sha256": "b41a0e699fd256738b13a9416afd50436e4f31b39af13e79e6264d9250a031b6"},
+    "radius_count": {"warp_inst": 707143347 / 62500, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
+    "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
