@@ -163,13 +163,7 @@ __global__ void __launch_bounds__(256) k_batch_tree_count(const uint64_t* __rest
         const int64_t p0 = p0s[sg];
         const int64_t end = p0 + segs[sg].n;
         const int64_t ncap = segs[sg].ncap;
-        uint32_t c = 0;
-        if (j + ncap < end) {
-            const int first_new = j == p0 ? 0 : common_levels(keys[j - 1], keys[j]) + 1;
-            int deepest = common_levels(keys[j], keys[j + ncap]);
-            if (deepest > kLevels - 1) deepest = kLevels - 1;
-            if (deepest >= first_new) c = static_cast<uint32_t>(deepest - first_new + 1);
-        }
+        const uint32_t c = new_internal_cells(keys, j, p0, end, ncap);
         cnt[j] = c;
     }
 }

@@ -244,28 +244,13 @@ __global__ void __launch_bounds__(256) k_pack_points(const float* __restrict__ x
 
 // ---------------------------------------------------------------------------------
 // section 5.1: linear octree
-__global__ void __launch_bounds__(256) k_tree_count(const uint64_t* __restrict__ keys, int64_t n, int64_t ncap,
-                                                    uint32_t* __restrict__ n_internal) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint32_t c = 0;
-        if (i + ncap < n) {
-            const int first_new = i == 0 ? 0 : common_levels(keys[i - 1], keys[i]) + 1;
-            int deepest = common_levels(keys[i], keys[i + ncap]);
-            if (deepest > kLevels - 1) deepest = kLevels - 1;  // a level-21 cell is never split
-            if (deepest >= first_new) c = static_cast<uint32_t>(deepest - first_new + 1);
-        }
-        n_internal[i] = c;
-    }
-}
-
+// first: the exclusive scan of the new internal cells of every position (n + 1 entries)
 __global__ void __launch_bounds__(256) k_tree_emit(const uint64_t* __restrict__ keys, int64_t n,
-                                                   const uint32_t* __restrict__ n_internal,
                                                    const int64_t* __restrict__ first, uint64_t* __restrict__ ikey,
                                                    uint8_t* __restrict__ ilevel) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t c = n_internal[i];
+        const uint32_t c = static_cast<uint32_t>(first[i + 1] - first[i]);
         if (c == 0) continue;
         const int first_new = i == 0 ? 0 : common_levels(keys[i - 1], keys[i]) + 1;
         const uint64_t k = keys[i];
@@ -511,13 +496,11 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
             SFC_LAUNCH("pack_points", s, k_pack_points, grid, 256, 0, xyz, n, t->pts, (unsigned int*)nullptr);
         else
             SFC_LAUNCH("gather_points", s, k_gather_points, grid, 256, 0, xyz, n, t->perm, t->pts);
-        // section 5.1: count the internal cells first seen at each sorted point
-        uint32_t* cnt;
+        // section 5.1: the internal cells first seen at each sorted point, counted and scanned
+        // in one pass over the codes
         int64_t* first;
-        SFC_TRY(scratch.alloc(&cnt, n));
         SFC_TRY(scratch.alloc(&first, n + 1));
-        SFC_LAUNCH("tree_count", s, k_tree_count, grid, 256, 0, t->keys, n, static_cast<int64_t>(t->leaf_cap), cnt);
-        SFC_TRY(scan_u32_to_i64(cnt, first, n, s, scratch, &t->scal->bad));
+        SFC_TRY(scan_tree_counts(t->keys, n, static_cast<int64_t>(t->leaf_cap), first, s, scratch, &t->scal->bad));
         BuildScalars hs;
         SFC_CUDA(cudaMemcpyAsync(&n_int, first + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SFC_CUDA(cudaMemcpyAsync(&hs, t->scal, sizeof(BuildScalars), cudaMemcpyDeviceToHost, s));
@@ -547,7 +530,7 @@ static sfc_status build_octree(Octree* t, const float* xyz, cudaStream_t s) {
         SFC_TRY(scratch.alloc(&arrive, n_int));
         if (n_int > 0) {
             SFC_CUDA(cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * n_int, s));
-            SFC_LAUNCH("tree_emit", s, k_tree_emit, grid, 256, 0, t->keys, n, cnt, first, ikey, ilevel);
+            SFC_LAUNCH("tree_emit", s, k_tree_emit, grid, 256, 0, t->keys, n, first, ikey, ilevel);
             SFC_LAUNCH("tree_link", s, k_tree_link, grid_for(n_int, 256, 152 * 16), 256, 0, ikey, ilevel, n_int,
                        t->child, islot);
         }

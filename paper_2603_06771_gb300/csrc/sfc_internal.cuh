@@ -208,6 +208,10 @@ sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStre
 int64_t scan_tile_count(int64_t n);
 sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s,
                                     unsigned int* fault = nullptr);
+// The same scan over the new internal cells of every sorted position of one cloud
+// (new_internal_cells with ncap), computed from the sorted codes as they are read.
+sfc_status scan_tree_counts(const uint64_t* keys, int64_t n, int64_t ncap, int64_t* first, cudaStream_t s,
+                            Scratch& scratch, unsigned int* fault = nullptr);
 // All-points count pass of the radius search into caller buffers (counts: one entry per
 // point, tile_sums: scan_tile_count(n) entries); reads nnz back (one synchronisation).
 sfc_status radius_count_presized(const Octree* t, float r, int kern, cudaStream_t s, uint32_t* counts,
@@ -273,6 +277,23 @@ __device__ __forceinline__ int common_levels(uint64_t a, uint64_t b) {
     uint64_t x = a ^ b;
     if (x == 0) return kLevels;
     return (__clzll(static_cast<long long>(x)) - 1) / 3;
+}
+
+// Internal cells of the linear octree first met at sorted position i (section 5.1): a
+// cell is split when it holds more than ncap points, i.e. when the codes at i and i + ncap
+// share it; the new ones at i are those below the deepest level i shares with i - 1 (all
+// of them from the root at the start of the range), down to the deepest level i shares
+// with i + ncap (never level 21).  lo: the first position of the range, end: one past its last.
+__device__ __forceinline__ uint32_t cells_from(int first_new, uint64_t code, uint64_t code_ncap_on) {
+    int deepest = common_levels(code, code_ncap_on);
+    if (deepest > kLevels - 1) deepest = kLevels - 1;  // a level-21 cell is never split
+    return deepest >= first_new ? static_cast<uint32_t>(deepest - first_new + 1) : 0u;
+}
+__device__ __forceinline__ uint32_t new_internal_cells(const uint64_t* keys, int64_t i, int64_t lo, int64_t end,
+                                                       int64_t ncap) {
+    if (i + ncap >= end) return 0u;
+    const int first_new = i == lo ? 0 : common_levels(keys[i - 1], keys[i]) + 1;
+    return cells_from(first_new, keys[i], keys[i + ncap]);
 }
 
 // Mask of the code bits below level l (the 3 * (21 - l) low bits).

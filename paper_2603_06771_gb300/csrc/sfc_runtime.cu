@@ -235,9 +235,48 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ in, int64_t* __restrict__ out,
-                                                       int64_t n, uint64_t* __restrict__ look, int64_t tiles,
-                                                       unsigned int* fault, int vec) {
+// Inputs of the scan: an array of counts, or the new internal cells of sorted codes.
+struct CountsInput {
+    const uint32_t* in;
+    int vec;  // in is 16-byte aligned
+    __device__ __forceinline__ void load(int64_t base, int64_t n, uint32_t v[kScanItems]) const {
+        if (vec && base + kScanItems <= n) {
+#pragma unroll
+            for (int j = 0; j < kScanItems / 4; ++j) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(in + base) + j);
+                v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) v[j] = base + j < n ? in[base + j] : 0u;
+        }
+    }
+};
+
+struct TreeCountsInput {
+    const uint64_t* keys;
+    int64_t ncap;
+    __device__ __forceinline__ void load(int64_t base, int64_t n, uint32_t v[kScanItems]) const {
+        if (base + kScanItems + ncap < n && base > 0) {  // every position has its neighbours: each code read once
+            uint64_t k[kScanItems + 1], far[kScanItems];
+#pragma unroll
+            for (int j = 0; j <= kScanItems; ++j) k[j] = __ldg(keys + base - 1 + j);
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) far[j] = __ldg(keys + base + ncap + j);
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) v[j] = cells_from(common_levels(k[j], k[j + 1]) + 1, k[j + 1], far[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j)
+                v[j] = base + j < n ? new_internal_cells(keys, base + j, 0, n, ncap) : 0u;
+        }
+    }
+};
+
+template <class In>
+__global__ void __launch_bounds__(kScanThreads) k_scan(In in, int64_t* __restrict__ out, int64_t n,
+                                                       uint64_t* __restrict__ look, int64_t tiles, unsigned int* fault,
+                                                       int vec) {
     __shared__ uint32_t s_tile;
     __shared__ int64_t s_before;
     if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int*>(look + tiles), 1u);
@@ -246,17 +285,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     const int64_t base = tile * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     static_assert(kScanItems % 4 == 0, "whole 16-byte loads and stores per thread");
     uint32_t v[kScanItems];
+    in.load(base, n, v);
     const bool full = vec && base + kScanItems <= n;
-    if (full) {
-#pragma unroll
-        for (int j = 0; j < kScanItems / 4; ++j) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4*>(in + base) + j);
-            v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) v[j] = base + j < n ? in[base + j] : 0u;
-    }
     int64_t acc = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) acc += v[j];
@@ -314,17 +344,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
 
 int64_t scan_tile_count(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s,
-                                    unsigned int* fault) {
+template <class In>
+static sfc_status scan_impl(In in, int64_t* out, int64_t n, int64_t* look, cudaStream_t s, unsigned int* fault,
+                            int vec) {
     if (n == 0) {
         SFC_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return SFC_OK;
     }
     const int64_t words = scan_tile_count(n);
-    SFC_CUDA(cudaMemsetAsync(tile_sums, 0, sizeof(int64_t) * words, s));
-    SFC_LAUNCH("scan", s, k_scan, static_cast<unsigned int>(words - 1), kScanThreads, 0, in, out, n,
-               reinterpret_cast<uint64_t*>(tile_sums), words - 1, fault, (aligned16(in) && aligned16(out)) ? 1 : 0);
+    SFC_CUDA(cudaMemsetAsync(look, 0, sizeof(int64_t) * words, s));
+    SFC_LAUNCH("scan", s, k_scan<In>, static_cast<unsigned int>(words - 1), kScanThreads, 0, in, out, n,
+               reinterpret_cast<uint64_t*>(look), words - 1, fault, vec);
     return SFC_OK;
+}
+
+sfc_status scan_u32_to_i64_presized(const uint32_t* in, int64_t* out, int64_t n, int64_t* tile_sums, cudaStream_t s,
+                                    unsigned int* fault) {
+    const int vec = (aligned16(in) && aligned16(out)) ? 1 : 0;
+    return scan_impl(CountsInput{in, vec}, out, n, tile_sums, s, fault, vec);
 }
 
 sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& scratch,
@@ -332,6 +369,13 @@ sfc_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStre
     int64_t* look = nullptr;
     if (n > 0) SFC_TRY(scratch.alloc(&look, static_cast<size_t>(scan_tile_count(n))));
     return scan_u32_to_i64_presized(in, out, n, look, s, fault);
+}
+
+sfc_status scan_tree_counts(const uint64_t* keys, int64_t n, int64_t ncap, int64_t* first, cudaStream_t s,
+                            Scratch& scratch, unsigned int* fault) {
+    int64_t* look = nullptr;
+    if (n > 0) SFC_TRY(scratch.alloc(&look, static_cast<size_t>(scan_tile_count(n))));
+    return scan_impl(TreeCountsInput{keys, ncap}, first, n, look, s, fault, aligned16(first) ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------------
