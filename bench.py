@@ -52,18 +52,18 @@ L2_FLUSH_BYTES = 512 << 20
 # with the sha256 of the source file it was measured on (null once the source changes).
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 10M-point tile, k = 16 (profiles/)
-    "knn": {"bytes_per_launch": 190045440 + 1250285312, "sha256": "b41a0e699fd256738b13a9416afd50436e4f31b39af13e79e6264d9250a031b6"},
-    "radius_fill": {"bytes_per_launch": 3166582528 + 4249777920, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
-    "radius_count": {"bytes_per_launch": 309697024 + 912296448, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
+    "knn": {"bytes_per_launch": 191145984 + 1250382592, "sha256": "51c8a6a8cf18055376e50cfd48ca5b7cfe4172f1761a0710b3a6bdbc6c96d7ff"},
+    "radius_fill": {"bytes_per_launch": 3155717376 + 4238458880, "sha256": "1c00063f58f40fbe7c3fde014e85c4931210ed8d0da2630aba09371f3e580692"},
+    "radius_count": {"bytes_per_launch": 309096448 + 911621120, "sha256": "1c00063f58f40fbe7c3fde014e85c4931210ed8d0da2630aba09371f3e580692"},
 }
 
 
 # warp instructions per group of 32 centres of the dominant kernels (ncu
 # smsp__inst_executed.sum on the 2M-point tile, profiles/), keyed like the traffic
 NCU_INST_PER_GROUP = {
-    "knn": {"warp_inst": 1368283468 / 62500, "sha256": "b41a0e699fd256738b13a9416afd50436e4f31b39af13e79e6264d9250a031b6"},
-    "radius_count": {"warp_inst": 707143347 / 62500, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
-    "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "f442f1118d9d9cffc46daa13fc20d12bece236d07926f00c94df9ea76039dd1d"},
+    "knn": {"warp_inst": 1368283468 / 62500, "sha256": "51c8a6a8cf18055376e50cfd48ca5b7cfe4172f1761a0710b3a6bdbc6c96d7ff"},
+    "radius_count": {"warp_inst": 707143347 / 62500, "sha256": "1c00063f58f40fbe7c3fde014e85c4931210ed8d0da2630aba09371f3e580692"},
+    "radius_fill": {"warp_inst": 497206502 / 62500, "sha256": "1c00063f58f40fbe7c3fde014e85c4931210ed8d0da2630aba09371f3e580692"},
 }
 SMS, SMSP_PER_SM = 152, 4  # GB300: one warp instruction per sub-partition per cycle
 FP32_LANES_PER_SM = 128      # GB300: 4 sub-partitions x 32 FP32 lanes, one operation each per cycle
@@ -932,8 +932,12 @@ def main(argv=None):
         d_pts = torch.empty_like(pts)
         copier = torch.cuda.Stream()
 
+        copied = {}  # step -> event after its last copy
+
         def e2e_step(s):
             h = h_sets[s % 2]
+            if s - 2 in copied:  # at most two steps in flight: the buffers of step s - 2 are free again
+                copied.pop(s - 2).synchronize()
             flush.fill_(s)
             d_pts.copy_(h_xyz, non_blocking=True)
             tree = sfc.octree_build(d_pts, cfg["encoding"], leaf_capacity=cfg["leaf_capacity"])
@@ -956,6 +960,8 @@ def main(argv=None):
                 copier.wait_event(knn_done)
                 h["idx"].copy_(idx, non_blocking=True)
                 h["d2"].copy_(d2, non_blocking=True)
+                copied[s] = torch.cuda.Event()
+                copied[s].record(copier)
             for t in (row_ptr, cols, idx, d2):  # freed only after the copy stream has read them
                 t.record_stream(copier)
             tree.free()
