@@ -143,9 +143,10 @@ sfc_status radius_fill(sfc_octree h, const float* queries_xyz, int64_t n_queries
  * device memory.  The paper has no counterpart: this exists for callers that cannot let a
  * library allocate, such as an application that reserves its whole device memory budget
  * up front (an allocation inside the call could fail or disturb its pool) or a loop with a
- * hard latency budget.  The per-point counts and scan sums live in a file-scope __device__
- * array of the library (about 8 MiB, held by every GPU that loads the library until the
- * process exits) instead of device scratch.
+ * hard latency budget.  The per-point counts and the scan's per-tile words live in a
+ * file-scope __device__ array of the library (about 8 MiB, held by every GPU that loads the
+ * library until the process exits) instead of device scratch; each call clears the words
+ * that must start at zero.
  *   row_ptr  device, n_points + 1 int64, caller-owned; *nnz (host) receives the total.
  *   Same results as radius_count(h, NULL, 0, r, kern, ...).
  * Limits: at most radius_count_static_max_points() points (2^21), else SFC_ERR_TOO_LARGE.
