@@ -5,7 +5,7 @@
 // device budget up front and hands out fixed buffers (so any cudaMalloc/cudaMallocAsync
 // inside a call could fail or evict its own pool), or a loop with a hard latency budget in
 // which an allocation's occasional cost or failure is not acceptable.  radius_count needs
-// device scratch (one count per point and one sum per scan tile); this variant takes that
+// device scratch (one count per point, one look-back word per scan tile); this variant takes that
 // scratch from one file-scope __device__ array instead, so it allocates nothing.  The
 // caller still provides the outputs.
 //
@@ -27,7 +27,7 @@ namespace {
 // Largest number of points (rows) the static scratch serves.
 constexpr int64_t kStaticRows = int64_t(1) << 21;
 constexpr int64_t kStaticCountBytes = kStaticRows * sizeof(uint32_t);  // a multiple of 256
-constexpr int64_t kStaticTileBytes = 1024 * sizeof(int64_t);            // >= scan tiles of kStaticRows
+constexpr int64_t kStaticTileBytes = 1024 * sizeof(int64_t);            // >= scan words of kStaticRows
 constexpr int64_t kStaticBytes = kStaticCountBytes + kStaticTileBytes;
 
 static __device__ __align__(256) unsigned char g_radius_scratch[kStaticBytes];
