@@ -246,8 +246,11 @@ def test_radius_deterministic():
 
 # ----------------------------------------------------------------------------- kNN
 @pytest.mark.parametrize("enc", ENCS)
-@pytest.mark.parametrize("k", [1, 8, 16, 50])
+@pytest.mark.parametrize("k", [1, 8, 16, 32, 50, 64])
 def test_knn_all_points_uniform(k, enc):
+    """All-points kNN, every row: k = 8, 16, 32, 50 and 64 run the kernel copies with the
+    list size (and, for the sorted encodings, the seeding window) fixed at compile time,
+    k = 1 the copy with both known at run time."""
     p = oracle_pipeline("uniform131k", enc, 32)
     oidx, od2 = p.tree.knn(p.xyz, k)
     t = sfc.octree_build(dev(p.xyz), enc, leaf_capacity=32)
