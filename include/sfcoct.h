@@ -51,7 +51,9 @@ typedef enum {
     SFC_ERR_INVALID = 1,         /* bad argument: n < 0, k < 1, NaN radius, bad enum, ... */
     SFC_ERR_OOM = 2,             /* a device allocation failed */
     SFC_ERR_CUDA = 3,            /* a CUDA call failed; see sfc_last_error() */
-    SFC_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up (reserved) */
+    SFC_ERR_TIMEOUT = 4,         /* a bounded wait gave up: a tile of the sort or of a scan
+                                    waiting for the counts of earlier tiles (never expected;
+                                    the results are then wrong), or server_wait's timeout */
     SFC_ERR_TOO_LARGE = 5,       /* a size limit of this library is exceeded */
     SFC_ERR_NOT_DEVICE_PTR = 6,  /* a pointer that must be device memory is not */
     SFC_ERR_NOT_FINITE = 7,      /* a coordinate, or the cloud's extent, is NaN or infinite */
