@@ -473,7 +473,9 @@ def batch_main(args):
         torch.cuda.synchronize()
         sfc.profile_read()
         sfc.profile_enable(True)
+        torch.cuda.nvtx.range_push(f"{name}_step")  # lets ncu --nvtx-include "batch_step/" pick one step
         fn()
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         sfc.profile_enable(False)
         breakdown[name] = {k: round(ms, 3) for k, (c, ms) in sorted(sfc.profile_read().items(),
